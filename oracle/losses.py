@@ -1,0 +1,148 @@
+"""Oracle compositions of the workload losses (test infrastructure only).
+
+Built from the C oracle's operators; numpy does only elementwise work and
+reductions.
+
+* ``chain_loss``: for a single banded SPD precision Q (lower band, l),
+  ``loss = -1/2 b^T Q^{-1} b + 1/2 log det Q + 1/2 tr(band(Q^{-1}) W)`` with W a
+  symmetric band matrix of the same bandwidth, and its gradient with respect to
+  the lower stored entries of Q, composed per Table 1, Alg. 2 and Alg. 4.
+* ``matern_kl``: the KL term of Eq. 5 / Alg. 7 for a Matern-3/2 state-space
+  prior and a banded variational posterior (mean m, precision L_q L_q^T).
+
+Trace over lower band storage (reading of Eq. 5 and of the trace terms):
+``tr(A B) = sum_d0 A_jj B_jj + 2 sum_{d>=1} A[d, j] B[d, j]`` for symmetric A, B
+stored as lower bands, because each stored off-diagonal entry stands for two
+entries of the full matrix.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import (cholesky, cholesky_vjp, logdet, product, solve, solve_vjp, subset_inverse,
+               subset_inverse_vjp)
+
+
+def sym_weights(l1: int) -> np.ndarray:
+    """Per-diagonal multiplicity of a symmetric lower-band entry: 1 on d=0, 2 above."""
+    w = np.full((l1, 1), 2.0)
+    w[0] = 1.0
+    return w
+
+
+def trace_sym(A: np.ndarray, B: np.ndarray) -> float:
+    return float(np.sum(sym_weights(A.shape[0]) * A * B))
+
+
+def chain_loss(Q, b, W, grad: bool = True):
+    """Returns (loss, Qbar) with Qbar the stored-entry gradient (lower band)."""
+    L, info = cholesky(Q)
+    if info:
+        raise ValueError(f"not SPD (info={info})")
+    Y = solve(L, b, 0)
+    X = solve(L, Y, 1)                               # X = Q^{-1} b
+    S = subset_inverse(L)                            # band(Q^{-1})
+    ld = logdet(L)
+    loss = -0.5 * float(b @ X) + 0.5 * ld + 0.5 * trace_sym(S, W)
+    if not grad:
+        return loss, None
+    Xbar = -0.5 * b
+    Sbar = 0.5 * W * sym_weights(W.shape[0])
+    ldbar = 0.5
+    Lbar = subset_inverse_vjp(L, S, Sbar)            # Alg. 4
+    Ybar, Lb1 = solve_vjp(L, 1, X, Xbar)             # X = L^{-T} Y   (Table 1)
+    _bbar, Lb2 = solve_vjp(L, 0, Y, Ybar)            # Y = L^{-1} b   (Table 1)
+    Lbar = Lbar + Lb1 + Lb2
+    Lbar[0] += 2.0 * ldbar / L[0]                    # d(2 sum log L_ii)
+    Qbar = cholesky_vjp(L, Lbar)                     # Alg. 2
+    return loss, Qbar
+
+
+# ---------------------------------------------------------------------------
+# Matern-3/2 state-space prior (Sec. 2: state (f, f') interleaved gives lower
+# bandwidth 3).  Textbook SDE: lambda = sqrt(3)/ell,
+#   A(D) = exp(-lambda D) [[1 + lambda D, D], [-lambda^2 D, 1 - lambda D]]
+#   Pinf = diag(s2, lambda^2 s2),  Sigma(D) = Pinf - A Pinf A^T.
+# The precision of the stacked states x_0..x_{n-1} is M^T M with M block
+# lower-bidiagonal: M_00 = C_0^{-1}, M_kk = C_k^{-1}, M_{k,k-1} = -C_k^{-1} A_k,
+# where C_0 = chol(Pinf) and C_k = chol(Sigma(t_k - t_{k-1})).
+# ---------------------------------------------------------------------------
+
+def matern_transition(D, ell, s2):
+    lam = math.sqrt(3.0) / ell
+    e = np.exp(-lam * D)
+    A = np.empty(D.shape + (2, 2))
+    A[..., 0, 0] = e * (1.0 + lam * D)
+    A[..., 0, 1] = e * D
+    A[..., 1, 0] = -e * lam * lam * D
+    A[..., 1, 1] = e * (1.0 - lam * D)
+    Pinf = np.array([[s2, 0.0], [0.0, lam * lam * s2]])
+    Sig = Pinf - A @ Pinf @ np.swapaxes(A, -1, -2)
+    return A, Sig, Pinf
+
+
+def chol2(S):
+    """Lower Cholesky of a stack of 2x2 SPD matrices."""
+    c00 = np.sqrt(S[..., 0, 0])
+    c10 = S[..., 1, 0] / c00
+    c11 = np.sqrt(S[..., 1, 1] - c10 * c10)
+    Cm = np.zeros(S.shape)
+    Cm[..., 0, 0], Cm[..., 1, 0], Cm[..., 1, 1] = c00, c10, c11
+    return Cm
+
+
+def inv_lower2(Cm):
+    Ci = np.zeros(Cm.shape)
+    Ci[..., 0, 0] = 1.0 / Cm[..., 0, 0]
+    Ci[..., 1, 1] = 1.0 / Cm[..., 1, 1]
+    Ci[..., 1, 0] = -Cm[..., 1, 0] / (Cm[..., 0, 0] * Cm[..., 1, 1])
+    return Ci
+
+
+def matern_M_band(t, ell, s2):
+    """M in general band storage with (lo, up) = (3, 0), size N = 2n."""
+    n = t.shape[0]
+    N = 2 * n
+    D = np.diff(t)
+    A, Sig, Pinf = matern_transition(D, ell, s2)
+    Cs = np.concatenate([chol2(Pinf)[None], chol2(Sig)], axis=0)     # (n, 2, 2)
+    Ci = inv_lower2(Cs)                                               # diagonal blocks
+    Off = -(Ci[1:] @ A)                                               # sub-diagonal blocks
+    M = np.zeros((4, N))
+    # diagonal block k occupies rows/cols 2k, 2k+1 (lower triangular 2x2)
+    M[0, 0::2] = Ci[:, 0, 0]
+    M[0, 1::2] = Ci[:, 1, 1]
+    M[1, 0::2] = Ci[:, 1, 0]
+    # off-diagonal block for k >= 1: rows 2k, 2k+1; cols 2k-2, 2k-1
+    k = np.arange(1, n)
+    # entry (2k+a, 2k-2+c) -> diagonal index d = 2 + a - c, column 2k-2+c
+    for a in range(2):
+        for c in range(2):
+            d = 2 + a - c
+            M[d, 2 * k - 2 + c] = Off[:, a, c]
+    return M
+
+
+def matern_precision(t, ell, s2):
+    M = matern_M_band(t, ell, s2)
+    # Q_p = M^T M, projected to lower band 3 (it has exactly bandwidth 3)
+    return product(M, 3, 0, 1, M, 3, 0, 0, 3, 0)
+
+
+def matern_kl(t, ell, s2, Lq, m):
+    """KL(N(m, (Lq Lq^T)^{-1}) || N(0, Q_p^{-1})), Eq. 5 / Alg. 7 with m_p = 0."""
+    Qp = matern_precision(t, ell, s2)
+    Lp, info = cholesky(Qp)
+    if info:
+        raise ValueError(f"prior precision not SPD (info={info})")
+    Sq = subset_inverse(Lq)
+    N = Lq.shape[1]
+    tr = trace_sym(Sq, Qp)
+    # ||P(Lp^T, m_p - m_q)||^2 with m_p = 0
+    from . import band_matvec
+    v = band_matvec(Lp, 3, 0, 1, -np.asarray(m, dtype=np.float64))
+    quad = float(v @ v)
+    logs = 2.0 * float(np.sum(np.log(Lq[0]) - np.log(Lp[0])))
+    return 0.5 * (tr + logs + quad - N)
