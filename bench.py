@@ -1,0 +1,446 @@
+"""Benchmark: band entries/s of the fused forward + backward step of the
+banded operators (Cholesky, solves, log-det, subset inverse and their
+adjoints) on the uneven batch, batched vs plain, with its HBM roofline.
+
+Workload ("uneven batch", 4096 instances): n log-uniform in [1000, 65536],
+l uniform in {1, 2, 3, 5, 7}, k = 4 right-hand sides, FP32, seeded synthetic
+SPD bands Q = band(L0 L0^T) + 1e-3 I with N(0,1) right-hand sides and
+cotangents (Xbar, Sbar) and ldbar = 1/2.  One step = banded_gmm_forward +
+banded_gmm_backward over the whole batch.  Inputs (~4.3 GB) are larger than
+L2, so no flush is needed between steps.
+
+Output: one JSON line (rank 0).  `value` is device-timed (inputs resident in
+HBM, CUDA graph replay); `e2e` adds the pinned host->device copy of the
+step's inputs and the device->host read of the step's result (log-dets and
+info) through the same public API.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1902_10078_gb300 import workloads as W  # noqa: E402
+
+METRIC = "band entries/s fwd+bwd (chol/solve/subinv), batched vs plain; % of HBM roofline"
+UNIT = "entries/s"
+WORKLOAD = "uneven batch: 4096 instances, n log-uniform [1000, 65536], l in {1,2,3,5,7}, k=4 RHS, FP32"
+
+
+# --------------------------------------------------------------------------- inputs
+
+def _fill_worker(args):
+    """Generate instances [i0, i1); return their contiguous slices of the pools."""
+    i0, i1, seed, lay_state = args
+    from paper_1902_10078_gb300.batch import Layout
+    lay = Layout.__new__(Layout)
+    lay.__dict__.update(lay_state)
+    b0 = lay.band_off[i0]
+    b1 = lay.band_off[i1] if i1 < lay.count else lay.band_elems
+    r0 = lay.rhs_off[i0]
+    r1 = lay.rhs_off[i1] if i1 < lay.count else lay.rhs_elems
+    out = {"Q": np.zeros(b1 - b0, np.float32), "Sbar": np.zeros(b1 - b0, np.float32),
+           "B": np.zeros(r1 - r0, np.float32), "Xbar": np.zeros(r1 - r0, np.float32)}
+    for i in range(i0, i1):
+        ins = W.make_instance(lay.ns[i], lay.ls[i], lay.k, seed + i)
+        o, ld, rows = lay.band_off[i] - b0, lay.ld[i], lay.rows[i]
+        for key, a in (("Q", ins.Q), ("Sbar", ins.Sbar)):
+            out[key][o:o + rows * ld].reshape(rows, ld)[: a.shape[0], : lay.ns[i]] = a
+        o = lay.rhs_off[i] - r0
+        for key, a in (("B", ins.B), ("Xbar", ins.Xbar)):
+            out[key][o:o + lay.k * ld].reshape(lay.k, ld)[:, : lay.ns[i]] = a
+    return (b0, b1, r0, r1), out
+
+
+def generate(lay, seed, workers):
+    """Host pools Q, Sbar (band) and B, Xbar (RHS), generated by a spawn pool
+    (started before any CUDA use) over contiguous chunks of instances."""
+    import multiprocessing as mp
+    pools = {"Q": np.zeros(lay.band_elems, np.float32), "Sbar": np.zeros(lay.band_elems, np.float32),
+             "B": np.zeros(lay.rhs_elems, np.float32), "Xbar": np.zeros(lay.rhs_elems, np.float32)}
+    chunks = max(1, min(workers * 4, lay.count))
+    bounds = np.linspace(0, lay.count, chunks + 1).astype(int)
+    jobs = [(int(bounds[c]), int(bounds[c + 1]), seed, lay.__dict__) for c in range(chunks) if bounds[c + 1] > bounds[c]]
+
+    def put(res):
+        (b0, b1, r0, r1), out = res
+        pools["Q"][b0:b1] = out["Q"]
+        pools["Sbar"][b0:b1] = out["Sbar"]
+        pools["B"][r0:r1] = out["B"]
+        pools["Xbar"][r0:r1] = out["Xbar"]
+    if workers > 1:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for res in pool.imap_unordered(_fill_worker, jobs):
+                put(res)
+    else:
+        for j in jobs:
+            put(_fill_worker(j))
+    return pools
+
+
+# --------------------------------------------------------------------------- clocks
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+
+def algorithmic_bytes(lay, w=4):
+    """Two-call (forward | backward) algorithmic bytes per step.
+
+    forward : Q read, L write, S write (band); B read, X write (RHS)
+    backward: L read, S read, Sbar read, Qbar write (band); X read, Xbar read, Bbar write (RHS)
+    -> per instance w * n * (7 (l+1) + 5 k); fused floor w * n * (4 (l+1) + 4 k).
+    """
+    fwd = bwd = floor = 0
+    for n, l in zip(lay.ns, lay.ls):
+        fwd += w * n * (3 * (l + 1) + 2 * lay.k)
+        bwd += w * n * (4 * (l + 1) + 3 * lay.k)
+        floor += w * n * (4 * (l + 1) + 4 * lay.k)
+    return fwd, bwd, floor
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_ours(args, rank, world, device_index):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1902_10078_gb300 import batch as BT
+    from paper_1902_10078_gb300 import binding as B
+
+    count = args.count
+    ns, ls = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919)
+    lay = BT.Layout(ns, ls, args.k, B.BND_F32)
+    host = generate(lay, W.BASE_SEED + rank * count, args.workers)      # before any CUDA use
+    torch.cuda.set_device(device_index)
+    from paper_1902_10078_gb300 import build as bld
+    bld.build()
+    tuning = dict(seg_len=args.seg_len, warmup=args.warm)
+    plan = BT.Plan(lay, tuning)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    L, S, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool()
+    X, Bb = lay.rhs_pool(), lay.rhs_pool()
+    logdet = torch.empty(count, dtype=torch.float64, device="cuda")
+    info = torch.empty(count, dtype=torch.int32, device="cuda")
+    ldbar = torch.full((count,), 0.5, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        B.banded_gmm_forward(plan.handle, dev["Q"], dev["B"], L, X, S, logdet, info)
+
+    def bwd():
+        B.banded_gmm_backward(plan.handle, L, X, S, dev["Xbar"], dev["Sbar"], ldbar, Qb, Bb)
+
+    def step():
+        fwd()
+        bwd()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert int(info.abs().sum()) == 0, "non-SPD instance in the benchmark batch"
+    fixups = sum(B.bnd_plan_fixups(plan.handle, kk) for kk in range(6))
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(device_index)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+
+    # per-call durations (eager, events on the launching stream) for the roofline
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    ms_fwd = timed(fwd, max(2, args.steps // 2))
+    ms_bwd = timed(bwd, max(2, args.steps // 2))
+
+    # end to end: pinned host inputs -> device, step, log-dets back to the host
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+    ld_host = torch.empty(count, dtype=torch.float64).pin_memory()
+    info_host = torch.empty(count, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        for k in ("Q", "B", "Xbar", "Sbar"):
+            dev[k].copy_(pinned[k], non_blocking=True)
+        step()
+        ld_host.copy_(logdet, non_blocking=True)
+        info_host.copy_(info, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_reps = max(2, min(args.steps, 5))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e_reps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = a.elapsed_time(b) / e_reps
+    h2d = sum(pinned[k].numel() * 4 for k in ("Q", "B", "Xbar", "Sbar"))
+    d2h = count * 8 + count * 4
+
+    entries = int(sum(n * (l + 1) for n, l in zip(lay.ns, lay.ls)))
+    # max over ranks
+    t = torch.tensor([ms, ms_e2e, ms_fwd, ms_bwd], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, ms_e2e, ms_fwd, ms_bwd = [float(x) for x in t.tolist()]
+
+    plain = None
+    if args.plain and rank == 0:
+        plain = run_plain(args, lay, host, torch, B, BT)
+
+    launches_per_step = 4 if plan.chains == count else 8   # sweep (+ verify) kernels per fused call x 2
+    fwd_b, bwd_b, floor_b = algorithmic_bytes(lay)
+    return dict(lay=lay, plan=plan, ms=ms, ms_e2e=ms_e2e, ms_fwd=ms_fwd, ms_bwd=ms_bwd, entries=entries,
+                fwd_bytes=fwd_b, bwd_bytes=bwd_b, floor_bytes=floor_b, clocks=clk, h2d=h2d, d2h=d2h,
+                fixups=fixups, plain=plain, launches=launches_per_step * args.steps)
+
+
+def run_plain(args, lay, host, torch, B, BT):
+    """The same kernels, one instance per launch, on one stream, no graph: time
+    a fixed sample of instances and scale to the whole batch by band entries."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    idx = np.sort(rng.choice(lay.count, size=min(args.plain_sample, lay.count), replace=False))
+    t_total = 0.0
+    ent = 0
+    for i in idx:
+        sub = BT.Layout([lay.ns[i]], [lay.ls[i]], lay.k, lay.dtype)
+        plan = BT.Plan(sub, dict(seg_len=args.seg_len, warmup=args.warm))
+
+        def cut_band(key):
+            o, ld, rows = lay.band_off[i], lay.ld[i], lay.rows[i]
+            return torch.from_numpy(host[key][o:o + rows * ld].copy()).cuda()
+
+        def cut_rhs(key):
+            o, ld = lay.rhs_off[i], lay.ld[i]
+            return torch.from_numpy(host[key][o:o + lay.k * ld].copy()).cuda()
+        Q, Sb, Bm, Xb = cut_band("Q"), cut_band("Sbar"), cut_rhs("B"), cut_rhs("Xbar")
+        L, S, Qb = torch.empty_like(Q), torch.empty_like(Q), torch.empty_like(Q)
+        X, Bb = torch.empty_like(Bm), torch.empty_like(Bm)
+        ld = torch.empty(1, dtype=torch.float64, device="cuda")
+        inf = torch.empty(1, dtype=torch.int32, device="cuda")
+        ldb = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+
+        def one():
+            B.banded_gmm_forward(plan.handle, Q, Bm, L, X, S, ld, inf)
+            B.banded_gmm_backward(plan.handle, L, X, S, Xb, Sb, ldb, Qb, Bb)
+        one()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        one()
+        b.record()
+        torch.cuda.synchronize()
+        t_total += a.elapsed_time(b)
+        ent += lay.ns[i] * (lay.ls[i] + 1)
+        plan.close()
+    total_entries = sum(n * (l + 1) for n, l in zip(lay.ns, lay.ls))
+    ms_full = t_total * total_entries / ent
+    return {"value": total_entries / (ms_full * 1e-3), "unit": UNIT, "ms_per_step_scaled": ms_full,
+            "sample_instances": int(len(idx)), "note": "one instance per launch, same kernels, one stream, "
+            "no graph; timed on a fixed sample and scaled to the batch by band entries"}
+
+
+# --------------------------------------------------------------------------- oracle arm
+
+def cpu_baseline(args, sample_count=None):
+    import oracle as O
+    count = args.count
+    ns, ls = W.batched_shapes(count)
+    sample_count = sample_count or args.cpu_sample
+    rng = np.random.Generator(np.random.PCG64(11))
+    idx = np.sort(rng.choice(count, size=min(sample_count, count), replace=False))
+    insts = [W.make_instance(int(ns[i]), int(ls[i]), args.k, W.BASE_SEED + int(i)) for i in idx]
+    for ins in insts:                      # the CPU sees the same FP32-rounded inputs
+        ins.Q = ins.Q.astype(np.float32).astype(np.float64)
+        ins.B = ins.B.astype(np.float32).astype(np.float64)
+    O.lib()
+    t = time.perf_counter()
+    _, threads = O.batch_step(insts)
+    dt = time.perf_counter() - t
+    ent = sum(i.n * (i.l + 1) for i in insts)
+    return {"value": ent / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(insts)} of {count} instances ({ent} band entries), FP64 C oracle, "
+                      f"OpenMP over instances, {dt:.2f} s"}, dt
+
+
+# --------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--k", type=int, default=4)
+    ap.add_argument("--seg-len", type=int, default=1024)
+    ap.add_argument("--warm", type=int, default=64)
+    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--plain", type=int, default=1)
+    ap.add_argument("--plain-sample", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(max(args.warmup, 0)):
+            cpu_baseline(args, sample_count=max(8, args.cpu_sample // 8))
+        cb = None
+        for _ in range(args.steps):
+            cb, dt = cpu_baseline(args, sample_count=max(8, args.cpu_sample // 8))
+            steps.append(dt)
+        line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(steps), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "step": "bounded sample of the batch per step"},
+                "impl": "reference", "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample", "value")},
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    r = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    lay = r["lay"]
+    entries_all = r["entries"] * world
+    value = entries_all / (r["ms"] * 1e-3)
+    # dominant fused call and its algorithmic bytes per launch
+    if r["ms_bwd"] >= r["ms_fwd"]:
+        dom, dom_ms, dom_bytes = "banded_gmm_backward", r["ms_bwd"], r["bwd_bytes"]
+    else:
+        dom, dom_ms, dom_bytes = "banded_gmm_forward", r["ms_fwd"], r["fwd_bytes"]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    step_gbs = (r["fwd_bytes"] + r["bwd_bytes"]) / (r["ms"] * 1e-3) / 1e9
+    cb = None
+    if not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(args)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
+                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len, "warmup_rows": args.warm,
+                   "chains": r["plan"].chains, "warp_tasks": r["plan"].tasks, "graph": True,
+                   "l2": "inputs (~%.1f GB) exceed L2; no flush" % (r["h2d"] / 1e9),
+                   "parallelism": f"instances sharded per GPU (weak), dp{world}", "segment_fixups": r["fixups"]},
+        "e2e": {"value": entries_all / (r["ms_e2e"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"], "ms_per_step": r["ms_e2e"]},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "ms_per_launch": dom_ms,
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "step_gbs": step_gbs, "step_frac": step_gbs / peaks["hbm_gbs"],
+                     "fused_floor_frac": r["floor_bytes"] / (r["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "ms_forward": r["ms_fwd"], "ms_backward": r["ms_bwd"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "cpu_baseline": cb,
+    }
+    if r["plain"] is not None:
+        line["plain"] = r["plain"]
+        line["batched_vs_plain"] = value / r["plain"]["value"]
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * banded.h -- C ABI of the GB300 banded SPD operator library.
+ *
+ * The library implements the banded linear-algebra operators of Durrande et
+ * al., "Banded Matrix Operators for Gaussian Markov Models in the Automatic
+ * Differentiation Era" (arXiv 1902.10078), and their reverse-mode adjoints,
+ * as CUDA kernels for sm_103a.  Every entry point is batched: one call runs
+ * `count` independent instances of uneven order n and lower bandwidth l.
+ *
+ * ---------------------------------------------------------------------------
+ * Storage (Sec. 4.3).  A band matrix with lower/upper bandwidths (lo, up) is
+ * an (lo+up+1) x n array B' with  B[i, j] = B'[up + i - j][j]  (0-based
+ * reading of the paper's index formula).  Lower-banded operands (L, and the
+ * symmetric Q, S, Qbar, Sbar stored by their lower half) use up = 0:
+ *     B'[d][j] = B[j + d, j],   d = 0..l.
+ * Row d of B' is contiguous: element (d, j) of instance i lives at
+ *     pool[inst[i].band + d * inst[i].ld + j].
+ * Corner entries (j + d >= n for lower bands) are never read; outputs write 0
+ * there.  Every band operand of one call uses the same per-instance offset
+ * `band` and row stride `ld`; the caller sizes each instance's region for the
+ * tallest operand of the call (e.g. lo+up+1 rows for products).
+ *
+ * Right-hand sides are n x k column blocks: element (j, r) of instance i at
+ *     pool[inst[i].rhs + r * inst[i].ldr + j].
+ *
+ * Symmetric matrices (Q, S = band(Q^{-1})) are stored by their lower band;
+ * their gradients (Qbar, Sbar) are gradients with respect to these STORED
+ * entries, so an off-diagonal stored entry carries the derivative of both
+ * (i, j) and (j, i).
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions.
+ *  - Memory: the caller owns every device buffer.  The library never
+ *    allocates device memory and never synchronises the stream; each call
+ *    only enqueues kernels (and small memsets) on `stream`.
+ *  - Pointers: `inst` passed to bnd_plan_create is HOST memory; every data
+ *    pointer passed to an operator (pools, workspace, logdet, info) is DEVICE
+ *    memory.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - Inputs are never written.  Outputs must not alias inputs unless stated.
+ *  - Errors: host-side validation failures return BND_EINVAL / BND_EALIGN
+ *    before anything is enqueued; a failed launch returns BND_ECUDA.
+ *    Numerical failure of the Cholesky (a pivot that is not > 0) is reported
+ *    per instance in `info` (LAPACK pbtrf style), never by the return code.
+ *  - dtype: BND_F32 or BND_F64 for all floating-point pools of a plan; the
+ *    log-determinant is always returned in double precision.
+ *  - Thread safety: a plan may be used from one stream at a time (it owns the
+ *    workspace bound to it); distinct plans are independent.
+ */
+#ifndef BANDED_H
+#define BANDED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BND_OK = 0,
+    BND_EINVAL = 1,      /* invalid argument (sizes, strides, mode, unbound plan) */
+    BND_ENOTSPD = 2,     /* reserved: a host-visible summary of info != 0 */
+    BND_ECUDA = 3,       /* a CUDA launch or memset failed */
+    BND_ETIMEOUT = 4,    /* reserved: a bounded device wait gave up */
+    BND_EALIGN = 5       /* a pointer or stride violates the stated alignment */
+} bnd_status;
+
+typedef enum { BND_F32 = 0, BND_F64 = 1 } bnd_dtype;
+
+/* One instance of a batch (host array given to bnd_plan_create). */
+typedef struct {
+    int64_t n;      /* order of the matrix, n >= 1 */
+    int64_t band;   /* element offset of B'[0][0] in every band pool of a call */
+    int64_t ld;     /* row stride of B' in elements, ld >= n */
+    int64_t rhs;    /* element offset of the first RHS column in every RHS pool */
+    int64_t ldr;    /* column stride of the RHS block in elements, ldr >= n (ignored if k = 0) */
+    int32_t l;      /* lower bandwidth, 0 <= l <= 1024 */
+    int32_t reserved;
+} bnd_inst;
+
+/* Scheduling knobs (all optional; zero fields take the library defaults). */
+typedef struct {
+    int64_t seg_len;     /* rows per chain segment; long instances are split into segments
+                            run in parallel (0 = default, < 0 = never split) */
+    int32_t warmup;      /* warm-up rows of a speculative segment start (0 = default) */
+    int32_t blocks_per_sm; /* persistent-grid occupancy (0 = default) */
+} bnd_tuning;
+
+typedef struct bnd_plan bnd_plan;
+
+/* ---------------------------------------------------------------------------
+ * Plans.  A plan fixes the batch (instances, dtype, number of right-hand
+ * sides k) and precomputes the schedule on the host: every instance is cut
+ * into row segments ("chains") that run as independent lanes of the GPU;
+ * chains of equal bandwidth are grouped 32 to a warp; warp tasks are ordered
+ * longest first for the persistent kernels.  Segments of one instance start
+ * from a speculative warm-up and are checked bit for bit against their
+ * neighbour afterwards; a mismatch reruns that segment from its exact start
+ * state, so results never depend on the segmentation beyond rounding of the
+ * warm-up (which the check excludes).
+ *
+ * bnd_plan_create copies `inst` (HOST) and returns BND_EINVAL on a bad
+ * descriptor (n < 1, l < 0 or > 1024, ld < n, ldr < n when k > 0, k < 0 or
+ * k > 64, count < 0).  bnd_plan_workspace_bytes gives the device workspace the
+ * plan needs; bnd_plan_bind uploads the plan's tables into that caller-owned
+ * workspace on `stream` and returns once the copies are complete (it
+ * synchronises `stream`; it is a set-up call, not an operator); `ws` must be
+ * 256-byte aligned and stay allocated while the plan is used.  The workspace
+ * holds the schedule tables, per-segment state snapshots and scratch pools
+ * shaped like the band and RHS pools of the plan.  bnd_plan_destroy frees
+ * host memory only.
+ * ------------------------------------------------------------------------- */
+bnd_status bnd_plan_create(bnd_plan **plan, bnd_dtype dtype, int32_t count, const bnd_inst *inst,
+                           int32_t k, const bnd_tuning *tuning);
+size_t bnd_plan_workspace_bytes(const bnd_plan *plan);
+bnd_status bnd_plan_bind(bnd_plan *plan, void *ws, size_t ws_bytes, void *stream);
+void bnd_plan_destroy(bnd_plan *plan);
+/* Number of chains (lanes of work) and warp tasks of the plan (for reporting). */
+int64_t bnd_plan_chains(const bnd_plan *plan);
+int64_t bnd_plan_tasks(const bnd_plan *plan);
+/* Number of segments rerun by the verify pass of the last launch of the given
+ * sweep kind (0 = Cholesky forward sweep, 1 = subset-inverse sweep,
+ * 2 = subset-inverse adjoint sweep, 3 = Cholesky adjoint sweep, 4 = forward
+ * solve sweep, 5 = backward solve sweep).  Copies the counter into the HOST
+ * int64 *out and synchronises `stream`.  Diagnostic only. */
+bnd_status bnd_plan_fixups(const bnd_plan *plan, int32_t kind, int64_t *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * C: banded Cholesky, Alg. 1 (App. B) and Sec. 4.1.  Q (lower band, SPD) ->
+ * L with L L^T = Q, lower bandwidth l.  logdet[i] = log det Q_i =
+ * 2 sum_j log L_jj in double precision (nullable).  info[i] = 0 on success,
+ * else r+1 where r is the first row whose pivot is not > 0; rows >= r of L
+ * are then unspecified (NaN in practice).  info is required.
+ * ------------------------------------------------------------------------- */
+bnd_status banded_cholesky(const bnd_plan *plan, const void *Q, void *L, double *logdet,
+                           int32_t *info, void *stream);
+
+/* Cbar: reverse mode of C, Alg. 2 (App. B).  L, Lbar -> Qbar, the gradient
+ * with respect to the lower stored entries of Q.  ldbar (DEVICE, one double
+ * per instance, nullable) is the cotangent of logdet; it adds 2 ldbar / L_jj
+ * to the diagonal of Lbar before the sweep (d log det Q / d L_jj = 2 / L_jj).
+ * accumulate = 1 adds into Qbar instead of overwriting it. */
+bnd_status banded_cholesky_vjp(const bnd_plan *plan, const void *L, const void *Lbar, const double *ldbar,
+                               void *Qbar, int32_t accumulate, void *stream);
+
+/* S: triangular solve with the plan's k right-hand sides, Sec. 4.1.
+ * mode 0: X = L^{-1} B;  mode 1: X = L^{-T} B;  mode 2: X = (L L^T)^{-1} B.
+ * X must not alias B. */
+bnd_status banded_solve(const bnd_plan *plan, const void *L, const void *B, void *X, int32_t mode,
+                        void *stream);
+
+/* Sbar: reverse mode of S, Table 1 ("solve matrix-vector").  Given the forward
+ * output X and its cotangent Xbar:
+ *   mode 0 (X = L^{-1} B):  Bbar = L^{-T} Xbar,  Lbar -= band_l(Bbar X^T)
+ *   mode 1 (X = L^{-T} B):  Bbar = L^{-1} Xbar,  Lbar -= band_l(X Bbar^T)
+ *   mode 2 (X = Q^{-1} B):  the composition of the two with Y = L^T X.
+ * Bbar is written (nullable); Lbar is overwritten, or added to when
+ * accumulate = 1 (nullable). */
+bnd_status banded_solve_vjp(const bnd_plan *plan, const void *L, const void *X, const void *Xbar,
+                            int32_t mode, void *Bbar, void *Lbar, int32_t accumulate, void *stream);
+
+/* I: subset inverse, Alg. 3 (App. B) and Sec. 4.1 (Takahashi).  L -> S, the
+ * lower band of (L L^T)^{-1}. */
+bnd_status banded_subset_inverse(const bnd_plan *plan, const void *L, void *S, void *stream);
+
+/* Ibar: reverse mode of I, Alg. 4 (App. B).  L, S, Sbar -> Lbar, the gradient
+ * with respect to the stored entries of L; Sbar is the gradient with respect
+ * to the stored (lower) entries of S.  accumulate = 1 adds into Lbar. */
+bnd_status banded_subset_inverse_vjp(const bnd_plan *plan, const void *L, const void *S,
+                                     const void *Sbar, void *Lbar, int32_t accumulate, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Fused step of the precision-parameterised Gaussian models (Sec. 3): one
+ * forward sweep pair and one backward sweep pair over every instance.
+ *   forward : L = C(Q), logdet = log det Q, X = Q^{-1} B, S = I(L)
+ *   backward: given Xbar, Sbar (stored entries) and ldbar (DEVICE, one double
+ *             per instance, nullable = 0), the gradients Qbar (stored entries
+ *             of Q) and Bbar (nullable) of
+ *             <Xbar, X> + <Sbar, S> + sum_i ldbar_i * logdet_i,
+ *             composed per Table 1, Alg. 2 and Alg. 4.
+ * Needs k in {1, 2, 3, 4}.  The forward writes L, X, S (and keeps L^{-1} B in
+ * the workspace); the backward reads L, X, S.
+ * ------------------------------------------------------------------------- */
+bnd_status banded_gmm_forward(const bnd_plan *plan, const void *Q, const void *B, void *L, void *X,
+                              void *S, double *logdet, int32_t *info, void *stream);
+bnd_status banded_gmm_backward(const bnd_plan *plan, const void *L, const void *X, const void *S,
+                               const void *Xbar, const void *Sbar, const double *ldbar, void *Qbar,
+                               void *Bbar, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * P and O: products (Sec. 4.1).  These take the same plan (for n, offsets and
+ * strides); operand shapes are per call.
+ *
+ * banded_product: C = op(A) op(B) projected onto C's band (clo, cup), with
+ *   op(X) = X or X^T (transX = 0 / 1).  A has bandwidths (alo, aup), B has
+ *   (blo, bup).  C must not alias A or B.
+ * banded_outer:   C = band_{clo,cup}(M V^T) = band(sum_r m_r v_r^T) over the
+ *   plan's k right-hand-side columns of M and V.
+ * banded_matvec:  P = op(A) V for the plan's k columns.
+ * accumulate = 1 adds into the output.
+ * ------------------------------------------------------------------------- */
+bnd_status banded_product(const bnd_plan *plan, const void *A, int32_t alo, int32_t aup,
+                          int32_t transA, const void *B, int32_t blo, int32_t bup, int32_t transB,
+                          void *C, int32_t clo, int32_t cup, int32_t accumulate, void *stream);
+bnd_status banded_outer(const bnd_plan *plan, const void *M, const void *V, void *C, int32_t clo,
+                        int32_t cup, int32_t accumulate, void *stream);
+bnd_status banded_matvec(const bnd_plan *plan, const void *A, int32_t alo, int32_t aup,
+                         int32_t transA, const void *V, void *P, int32_t accumulate, void *stream);
+
+/* Pbar: Table 1 ("product matrix-matrix"), band-projected (Sec. 4.2):
+ *   Abar = band_A(Cbar op(B)^T)  (or its transpose when transA),
+ *   Bbar = band_B(op(A)^T Cbar)  (or its transpose when transB).
+ * Either output may be NULL.  accumulate = 1 adds into the outputs. */
+bnd_status banded_product_vjp(const bnd_plan *plan, const void *A, int32_t alo, int32_t aup,
+                              int32_t transA, const void *B, int32_t blo, int32_t bup,
+                              int32_t transB, const void *Cbar, int32_t clo, int32_t cup,
+                              void *Abar, void *Bbar, int32_t accumulate, void *stream);
+
+/* Library version string (static storage). */
+const char *bnd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BANDED_H */

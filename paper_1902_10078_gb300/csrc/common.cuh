@@ -1,0 +1,110 @@
+// Shared definitions of the banded-operator CUDA library (device and host).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/banded.h"
+
+namespace bnd {
+
+constexpr int kWarp = 32;
+constexpr int kRegMaxL = 8;        // bandwidths 1..kRegMaxL run the register-window kernels
+constexpr int kMaxK = 4;           // right-hand sides per register-window sweep
+
+// One chain: the rows [a, b) of one instance, run by one lane.  The lane
+// starts its recurrence `warm` rows before a (forward sweeps) or after b
+// (backward sweeps) from a cold state; only rows in [a, b) are written.
+struct Chain {
+    int32_t inst;      // instance index, -1 for an idle padding lane
+    int32_t seg;       // segment index within the instance (0 = first row block)
+    int64_t a, b;      // output rows [a, b)
+};
+
+// Per-instance data uploaded to the workspace.
+struct InstDev {
+    int64_t n, band, ld, rhs, ldr;
+    int32_t l;
+    int32_t nseg;      // number of row segments
+    int64_t seg0;      // global id of the instance's first segment (ids are consecutive)
+    int64_t seg_len;   // rows per segment (the last one may be shorter)
+};
+
+// A warp task: 32 consecutive entries of the chain table (all the same l).
+struct Task {
+    int32_t chain0;    // first chain index
+    int32_t l;         // bandwidth shared by the task's chains
+};
+
+// Sweep kinds (for state snapshots and fixup counters).
+enum SweepKind : int32_t { kSweepChol = 0, kSweepTaka = 1, kSweepTakaBar = 2, kSweepCholBar = 3,
+                           kSweepFSolve = 4, kSweepBSolve = 5, kNumSweepKinds = 6 };
+
+// Device view of a bound plan.
+struct PlanDev {
+    const InstDev *inst;
+    const Chain *chains;
+    const Task *tasks;
+    const int64_t *tile_prefix;  // products: prefix of 256-column tiles per instance
+    int64_t ntiles;
+    int32_t ntasks;
+    int32_t count;
+    int64_t nchains;
+    int32_t k;
+    int32_t warm;
+    // workspace areas
+    int64_t nsegs;
+    uint32_t *counters;      // [2 * kNumSweepKinds]: task queue heads, then fixup counters
+    void *snap;              // per segment: 2 snapshots (start, end) of snap_words elements
+    int64_t snap_words;
+    double *seg_logdet;      // per segment partial log-det
+    int32_t *seg_info;       // per segment first failing row + 1 (0 = none)
+    void *rhs_tmp;           // RHS-shaped scratch pool
+    void *rhs_tmp2;          // second RHS-shaped scratch pool
+    void *band_tmp;          // band-shaped scratch pool (fused backward intermediate)
+    void *band_tmp2;         // band-shaped scratch pools of the generic (wide band) path
+    void *band_tmp3;
+};
+
+__host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// Size in elements of the per-chain state snapshot for bandwidth l and k RHS.
+__host__ __device__ inline int64_t snap_words_for(int l, int k) {
+    // the largest sweep state: Schur window l(l+1)/2 + pending RHS l*k (+1 guard)
+    int64_t t = (int64_t)l * (l + 1) / 2;
+    return 2 * t + 2 * (int64_t)l * k + 8;
+}
+
+}  // namespace bnd
+
+// Host-side plan (defined in plan.cpp, used by abi.cu).
+struct bnd_plan {
+    bnd_dtype dtype;
+    int32_t count;
+    int32_t k;
+    int32_t warm;
+    int64_t seg_len;
+    int32_t blocks_per_sm;
+    int32_t max_l;
+    int64_t nchains;
+    int64_t nsegs;
+    int32_t ntasks;
+    int64_t snap_words;
+    int64_t band_pool_elems;   // extent of a band pool implied by the instances
+    int64_t rhs_pool_elems;    // extent of an RHS pool implied by the instances
+    // host tables
+    bnd::InstDev *inst;
+    bnd::Chain *chains;
+    bnd::Task *tasks;
+    int64_t *tile_prefix;
+    int64_t ntiles;
+    int32_t has_generic;       // some instance runs the generic (any-bandwidth) path
+    // workspace layout (byte offsets)
+    size_t off_inst, off_chains, off_tasks, off_tiles, off_counters, off_snap, off_logdet, off_info,
+        off_rhs_tmp, off_rhs_tmp2, off_band_tmp, off_band_tmp2, off_band_tmp3, ws_bytes;
+    // bound workspace
+    void *ws;
+    bnd::PlanDev dev;
+    int bound;
+};

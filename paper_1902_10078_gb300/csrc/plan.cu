@@ -1,0 +1,229 @@
+// Host-side plan: validation, segmentation of long instances into chains,
+// grouping of equal-bandwidth chains into warp tasks, longest-first task
+// order, and the device workspace layout.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace bnd;
+
+namespace {
+
+constexpr int64_t kDefaultSegLen = 1024;
+constexpr int32_t kDefaultWarmF32 = 64;
+constexpr int32_t kDefaultWarmF64 = 128;
+constexpr int32_t kMaxBand = 1024;
+constexpr int32_t kMaxRhs = 64;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t count, const bnd_inst *inst,
+                                      int32_t k, const bnd_tuning *tuning) {
+    if (!out) return BND_EINVAL;
+    *out = nullptr;
+    if (dtype != BND_F32 && dtype != BND_F64) return BND_EINVAL;
+    if (count < 0 || (count > 0 && !inst)) return BND_EINVAL;
+    if (k < 0 || k > kMaxRhs) return BND_EINVAL;
+    for (int32_t i = 0; i < count; ++i) {
+        const bnd_inst &I = inst[i];
+        if (I.n < 1 || I.l < 0 || I.l > kMaxBand || I.ld < I.n || I.band < 0) return BND_EINVAL;
+        if (k > 0 && (I.ldr < I.n || I.rhs < 0)) return BND_EINVAL;
+    }
+    bnd_plan *p = new (std::nothrow) bnd_plan();
+    if (!p) return BND_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->dtype = dtype;
+    p->count = count;
+    p->k = k;
+    const size_t esz = dtype == BND_F32 ? 4 : 8;
+    p->warm = dtype == BND_F32 ? kDefaultWarmF32 : kDefaultWarmF64;
+    p->seg_len = kDefaultSegLen;
+    if (tuning) {
+        if (tuning->seg_len != 0) p->seg_len = tuning->seg_len;
+        if (tuning->warmup > 0) p->warm = tuning->warmup;
+        if (tuning->blocks_per_sm > 0) p->blocks_per_sm = tuning->blocks_per_sm;
+    }
+
+    std::vector<InstDev> idev((size_t)count);
+    int64_t nsegs = 0;
+    int32_t max_l = 0;
+    bool has_generic = false;
+    int64_t band_extent = 0, rhs_extent = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const bnd_inst &I = inst[i];
+        InstDev &D = idev[(size_t)i];
+        D.n = I.n; D.band = I.band; D.ld = I.ld; D.rhs = I.rhs; D.ldr = I.ldr; D.l = I.l;
+        const bool reg = I.l >= 1 && I.l <= kRegMaxL;
+        if (!reg) has_generic = true;
+        int64_t nseg = 1;
+        if (reg && p->seg_len > 0 && I.n > p->seg_len + p->warm) {
+            nseg = (I.n + p->seg_len / 2) / p->seg_len;     // nearest segment count
+            if (nseg < 1) nseg = 1;
+        }
+        int64_t len = (I.n + nseg - 1) / nseg;
+        len = (len + 3) / 4 * 4;                              // multiple of 4 rows
+        nseg = (I.n + len - 1) / len;
+        D.nseg = (int32_t)nseg;
+        D.seg_len = len;
+        D.seg0 = nsegs;
+        nsegs += nseg;
+        max_l = std::max(max_l, I.l);
+        band_extent = std::max(band_extent, I.band + (int64_t)(I.l + 1) * I.ld);
+        if (k > 0) rhs_extent = std::max(rhs_extent, I.rhs + (int64_t)k * I.ldr);
+    }
+    p->nsegs = nsegs;
+    p->max_l = max_l;
+    p->band_pool_elems = band_extent;
+    p->rhs_pool_elems = rhs_extent;
+    p->snap_words = snap_words_for(std::min(max_l, kRegMaxL), std::max(k, kMaxK));
+
+    // chains: one per segment, grouped by l, longest first inside a group
+    std::vector<Chain> ch;
+    ch.reserve((size_t)nsegs);
+    for (int32_t i = 0; i < count; ++i) {
+        const InstDev &D = idev[(size_t)i];
+        for (int32_t s = 0; s < D.nseg; ++s) {
+            Chain c;
+            c.inst = i; c.seg = s;
+            c.a = (int64_t)s * D.seg_len;
+            c.b = std::min(c.a + D.seg_len, D.n);
+            ch.push_back(c);
+        }
+    }
+    std::stable_sort(ch.begin(), ch.end(), [&](const Chain &x, const Chain &y) {
+        const int lx = idev[(size_t)x.inst].l, ly = idev[(size_t)y.inst].l;
+        if (lx != ly) return lx < ly;
+        return (x.b - x.a) > (y.b - y.a);
+    });
+    // tasks of 32 chains with equal l
+    struct TaskTmp { std::vector<Chain> c; int32_t l; double cost; };
+    std::vector<TaskTmp> tt;
+    for (size_t s = 0; s < ch.size();) {
+        const int32_t l = idev[(size_t)ch[s].inst].l;
+        TaskTmp t;
+        t.l = l;
+        t.cost = 0;
+        while (s < ch.size() && (int)t.c.size() < kWarp && idev[(size_t)ch[s].inst].l == l) {
+            const Chain &c = ch[s];
+            int64_t rows = c.b - c.a + (c.seg > 0 ? p->warm : 0);
+            t.cost = std::max(t.cost, (double)rows * (double)(l + 2) * (double)(l + 2));
+            t.c.push_back(c);
+            ++s;
+        }
+        while ((int)t.c.size() < kWarp) { Chain pad; pad.inst = -1; pad.seg = 0; pad.a = pad.b = 0; t.c.push_back(pad); }
+        tt.push_back(std::move(t));
+    }
+    std::stable_sort(tt.begin(), tt.end(), [](const TaskTmp &x, const TaskTmp &y) { return x.cost > y.cost; });
+    p->ntasks = (int32_t)tt.size();
+    p->nchains = (int64_t)tt.size() * kWarp;
+    p->inst = (InstDev *)std::malloc(sizeof(InstDev) * std::max<size_t>(1, (size_t)count));
+    p->chains = (Chain *)std::malloc(sizeof(Chain) * std::max<size_t>(1, (size_t)p->nchains));
+    p->tasks = (Task *)std::malloc(sizeof(Task) * std::max<size_t>(1, tt.size()));
+    if (!p->inst || !p->chains || !p->tasks) { bnd_plan_destroy(p); return BND_EINVAL; }
+    if (count) std::memcpy(p->inst, idev.data(), sizeof(InstDev) * (size_t)count);
+    for (size_t t = 0; t < tt.size(); ++t) {
+        p->tasks[t].chain0 = (int32_t)(t * kWarp);
+        p->tasks[t].l = tt[t].l;
+        for (int c = 0; c < kWarp; ++c) p->chains[t * kWarp + c] = tt[t].c[(size_t)c];
+    }
+    // product tile prefix (256 columns per tile)
+    p->tile_prefix = (int64_t *)std::malloc(sizeof(int64_t) * ((size_t)count + 1));
+    if (!p->tile_prefix) { bnd_plan_destroy(p); return BND_EINVAL; }
+    p->tile_prefix[0] = 0;
+    for (int32_t i = 0; i < count; ++i) p->tile_prefix[i + 1] = p->tile_prefix[i] + (idev[(size_t)i].n + 255) / 256;
+    p->ntiles = p->tile_prefix[count];
+    p->has_generic = has_generic ? 1 : 0;
+
+    // workspace layout
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    p->off_inst = take(sizeof(InstDev) * (size_t)count);
+    p->off_chains = take(sizeof(Chain) * (size_t)p->nchains);
+    p->off_tasks = take(sizeof(Task) * (size_t)p->ntasks);
+    p->off_tiles = take(sizeof(int64_t) * ((size_t)count + 1));
+    p->off_counters = take(sizeof(unsigned int) * 2 * kNumSweepKinds);
+    p->off_snap = take(esz * (size_t)nsegs * 2 * (size_t)p->snap_words);
+    p->off_logdet = take(sizeof(double) * (size_t)nsegs);
+    p->off_info = take(sizeof(int32_t) * (size_t)nsegs);
+    p->off_rhs_tmp = take(esz * (size_t)rhs_extent);
+    p->off_rhs_tmp2 = take(esz * (size_t)rhs_extent);
+    p->off_band_tmp = take(esz * (size_t)band_extent);
+    p->off_band_tmp2 = take(has_generic ? esz * (size_t)band_extent : 0);
+    p->off_band_tmp3 = take(has_generic ? esz * (size_t)band_extent : 0);
+    p->ws_bytes = o;
+    *out = p;
+    return BND_OK;
+}
+
+extern "C" size_t bnd_plan_workspace_bytes(const bnd_plan *p) { return p ? p->ws_bytes : 0; }
+
+extern "C" int64_t bnd_plan_chains(const bnd_plan *p) { return p ? p->nsegs : 0; }
+
+extern "C" int64_t bnd_plan_tasks(const bnd_plan *p) { return p ? p->ntasks : 0; }
+
+extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || (!ws && p->ws_bytes) || ws_bytes < p->ws_bytes) return BND_EINVAL;
+    if (((uintptr_t)ws & 255) != 0) return BND_EALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = (char *)ws;
+    p->ws = ws;
+    PlanDev &d = p->dev;
+    d.inst = (const InstDev *)(base + p->off_inst);
+    d.chains = (const Chain *)(base + p->off_chains);
+    d.tasks = (const Task *)(base + p->off_tasks);
+    d.tile_prefix = (const int64_t *)(base + p->off_tiles);
+    d.ntasks = p->ntasks;
+    d.count = p->count;
+    d.nchains = p->nchains;
+    d.nsegs = p->nsegs;
+    d.ntiles = p->ntiles;
+    d.k = p->k;
+    d.warm = p->warm;
+    d.counters = (unsigned int *)(base + p->off_counters);
+    d.snap = base + p->off_snap;
+    d.snap_words = p->snap_words;
+    d.seg_logdet = (double *)(base + p->off_logdet);
+    d.seg_info = (int32_t *)(base + p->off_info);
+    d.rhs_tmp = base + p->off_rhs_tmp;
+    d.rhs_tmp2 = base + p->off_rhs_tmp2;
+    d.band_tmp = base + p->off_band_tmp;
+    d.band_tmp2 = base + p->off_band_tmp2;
+    d.band_tmp3 = base + p->off_band_tmp3;
+    cudaError_t e = cudaSuccess;
+    if (p->count) e = cudaMemcpyAsync(base + p->off_inst, p->inst, sizeof(InstDev) * (size_t)p->count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && p->nchains) e = cudaMemcpyAsync(base + p->off_chains, p->chains, sizeof(Chain) * (size_t)p->nchains, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && p->ntasks) e = cudaMemcpyAsync(base + p->off_tasks, p->tasks, sizeof(Task) * (size_t)p->ntasks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + p->off_tiles, p->tile_prefix, sizeof(int64_t) * ((size_t)p->count + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + p->off_counters, 0, sizeof(unsigned int) * 2 * kNumSweepKinds, s);
+    // pageable sources: make sure the copies have consumed the host tables before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return BND_ECUDA;
+    p->bound = 1;
+    return BND_OK;
+}
+
+extern "C" void bnd_plan_destroy(bnd_plan *p) {
+    if (!p) return;
+    std::free(p->inst);
+    std::free(p->chains);
+    std::free(p->tasks);
+    std::free(p->tile_prefix);
+    delete p;
+}
+
+extern "C" bnd_status bnd_plan_fixups(const bnd_plan *p, int32_t kind, int64_t *out, void *stream) {
+    if (!p || !p->bound || !out || kind < 0 || kind >= kNumSweepKinds) return BND_EINVAL;
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, p->dev.counters + kNumSweepKinds + kind, sizeof(v), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return BND_ECUDA;
+    *out = v;
+    return BND_OK;
+}

@@ -1,0 +1,10 @@
+// fwd sweeps, float.
+#include "sweep_launch.cuh"
+#include "products.cuh"
+
+namespace bnd {
+template <>
+cudaError_t launch_fwd<float>(const bnd_plan *p, int fl, int K, const SweepArgs<float> &A, cudaStream_t s) {
+    return dispatch_fwd<float>(p, fl, K, A, s);
+}
+}  // namespace bnd

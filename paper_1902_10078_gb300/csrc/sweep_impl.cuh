@@ -1,0 +1,712 @@
+// Sequential-in-n band sweeps of the banded operators (register-window and
+// generic forms).  Included by the per-dtype translation units.
+//
+// Every sweep walks the columns of one chain (a row segment of one instance)
+// in one direction and carries a small window of state in registers:
+//
+//   forward sweeps (j ascending)
+//     CHOL  : Cholesky, Alg. 1, in column (left-looking, pending-sum) order:
+//             a_d = Q[j+d, j] - sum_{m<j} L[j+d, m] L[j, m]; L_jj = sqrt(a_0);
+//             L[j+d, j] = a_d / L_jj.  Same entries and formulas as Alg. 1;
+//             only the order in which entries are produced differs.
+//     SOLVE : y = L^{-1} b in column (axpy) order.
+//     ALG4  : reverse mode of the subset inverse (Alg. 4), taken as the exact
+//             reverse of the row-ordered Takahashi recursion below; the pair
+//             adjoints of the symmetric S are one value per unordered pair
+//             (i, j), seeded with the gradient of the stored entry.
+//   backward sweeps (j descending)
+//     TAKA  : subset inverse, Alg. 3, in row order: for i descending,
+//             Sym[i, i+q] = -sum_t U[i, i+t] Sym[i+t, i+q] (q = l..1), then
+//             Sym[i, i] = 1/L_ii^2 - sum_t U[i, i+t] Sym[i, i+t],
+//             U[i, m] = L[m, i] / L_ii.  Same recursion as Alg. 3.
+//     SOLVE : x = L^{-T} y (dot order).
+//     ALG2  : reverse mode of the Cholesky (Alg. 2) in column-reverse order,
+//             with the Table-1 solve adjoint outer products and the log-det
+//             term added to Lbar of each column before it is consumed.
+//
+// Long instances are split into segments.  A segment whose start is not the
+// instance's boundary starts `warm` columns early from a cold (zero) state;
+// the state entering its first output column is saved ("start snapshot"),
+// and the state after its last output column likewise ("end snapshot").  A
+// verify pass compares neighbours bit for bit and reruns mismatching
+// segments from the exact end snapshot of their predecessor.
+#pragma once
+
+#include "common.cuh"
+
+namespace bnd {
+
+// ---------------------------------------------------------------------------
+// Flags
+// ---------------------------------------------------------------------------
+enum : int { F_CHOL = 1, F_SOLVE = 2, F_ALG4 = 4 };
+enum : int { B_TAKA = 1, B_SOLVE = 2, B_ALG2 = 4, B_OUTER = 8 };
+
+template <typename T>
+struct SweepArgs {
+    const T *Q;          // CHOL input
+    T *L;                // CHOL output
+    const T *Lin;        // L input of every other sweep
+    const T *S;          // ALG4 input
+    const T *Sbar;       // ALG4 input
+    T *Sout;             // TAKA output
+    T *Lbar;             // ALG4 output (accumulated when acc)
+    const T *Lbar_in;    // ALG2 input
+    T *Qbar;             // ALG2 output (accumulated when acc)
+    T *scratch;          // generic path band scratch 1 (zeroed before the launch)
+    T *scratch2;         // generic path band scratch 2
+    const T *Bin;        // SOLVE input (B or Y)
+    T *Xout;             // SOLVE output
+    const T *Xin;        // ALG2+OUTER: forward output X (Y = L^T X)
+    const T *Ybar;       // ALG2+OUTER: Ybar (= Bin of the fused backward)
+    int32_t rhs0;        // first RHS column handled by this launch
+    int32_t kk;          // RHS columns handled by this launch (<= the kernel's K)
+    int32_t acc;         // accumulate into Lbar / Qbar
+    const double *ldbar; // ALG2: per-instance log-det cotangent (nullable)
+    double *logdet;      // CHOL: per-instance log det (final)
+    int32_t *info;       // CHOL: per-instance info (final)
+    int32_t kind;        // SweepKind of this launch (snapshots, counters)
+};
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+};
+
+// Index of the unordered pair (a, b), 0 <= a, b < L, in a packed triangle.
+__host__ __device__ constexpr int tri(int a, int b, int L) {
+    return (a <= b) ? (a * L - (a * (a - 1)) / 2 + (b - a)) : (b * L - (b * (b - 1)) / 2 + (a - b));
+}
+template <int L> struct Tri { static constexpr int N = L * (L + 1) / 2; };
+
+// Per-chain context: instance view plus the segment's rows.
+struct ChainCtx {
+    int64_t n, band, ld, rhs, ldr;
+    int64_t a, b;        // output rows [a, b)
+    int64_t gseg;        // global segment id
+    int32_t inst;        // instance index
+    int32_t l;
+    bool first, last;    // first / last segment of the instance
+};
+
+template <typename T>
+__device__ __forceinline__ T *snap_ptr(const PlanDev &P, int64_t gseg, int which) {
+    return reinterpret_cast<T *>(P.snap) + (gseg * 2 + which) * P.snap_words;
+}
+
+// Bitwise equality of two state snapshots.
+template <typename T>
+__device__ inline bool snap_equal(const T *x, const T *y, int64_t words) {
+    bool eq = true;
+    for (int64_t w = 0; w < words; ++w) {
+        if (sizeof(T) == 4) eq &= (__float_as_uint((float)x[w]) == __float_as_uint((float)y[w]));
+        else eq &= (__double_as_longlong((double)x[w]) == __double_as_longlong((double)y[w]));
+    }
+    return eq;
+}
+
+// Start modes of a chain run.
+enum : int { RUN_COLD = 0, RUN_EXACT = 1 };
+
+// ===========================================================================
+// Register-window forward sweep: CHOL [+ SOLVE], SOLVE, ALG4 [+ SOLVE]
+// ===========================================================================
+template <typename T, int L, int K, int FL>
+struct FwdReg {
+    static constexpr int NT = Tri<L>::N;
+    static constexpr bool CHOL = (FL & F_CHOL) != 0;
+    static constexpr bool SOLVE = (FL & F_SOLVE) != 0 && K > 0;
+    static constexpr bool ALG4 = (FL & F_ALG4) != 0;
+    static constexpr int KK = SOLVE ? K : 1;
+    // computed state
+    T pw[NT];           // CHOL: pending Schur sums, pair (c-j, r-j) in [0, L-1]
+    T pend[NT];         // ALG4: pending pair adjoints, pair (t, q) relative to i, in [0, L-1]
+    T u[KK][L];         // SOLVE: pending sums for rows j..j+L-1
+    // input-derived state
+    T sblk[NT];         // ALG4: Sigma block of rows/cols i+1..i+L, pair (t-1, q-1)
+
+    static constexpr int snap_words() { return (CHOL ? NT : 0) + (ALG4 ? NT : 0) + (SOLVE ? K * L : 0); }
+
+    __device__ void save(T *dst) const {
+        int o = 0;
+        if (CHOL) { _Pragma("unroll") for (int x = 0; x < NT; ++x) dst[o++] = pw[x]; }
+        if (ALG4) { _Pragma("unroll") for (int x = 0; x < NT; ++x) dst[o++] = pend[x]; }
+        if (SOLVE) { _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) dst[o++] = u[r][d]; }
+    }
+    __device__ void load_state(const T *src) {
+        int o = 0;
+        if (CHOL) { _Pragma("unroll") for (int x = 0; x < NT; ++x) pw[x] = src[o++]; }
+        if (ALG4) { _Pragma("unroll") for (int x = 0; x < NT; ++x) pend[x] = src[o++]; }
+        if (SOLVE) { _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) u[r][d] = src[o++]; }
+    }
+    __device__ void zero() {
+        _Pragma("unroll") for (int x = 0; x < NT; ++x) { pw[x] = T(0); pend[x] = T(0); sblk[x] = T(0); }
+        _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) u[r][d] = T(0);
+    }
+
+    // Preload the ALG4 Sigma block for iteration i0: Sigma[i0+t, i0+q], 1 <= t <= q <= L.
+    __device__ void preload(const SweepArgs<T> &A, const ChainCtx &c, int64_t i0) {
+        if (!ALG4) return;
+        const T *S = A.S + c.band;
+        _Pragma("unroll") for (int t = 1; t <= L; ++t)
+            _Pragma("unroll") for (int q = t; q <= L; ++q) {
+                int64_t col = i0 + t, row = i0 + q;
+                sblk[tri(t - 1, q - 1, L)] = (row < c.n) ? S[(int64_t)(q - t) * c.ld + col] : T(0);
+            }
+    }
+
+    // One column / row step.  `out` selects whether outputs are written.
+    __device__ __forceinline__ void step(const SweepArgs<T> &A, const ChainCtx &c, int64_t j, bool out,
+                                         double &ldacc, int32_t &info) {
+        const int64_t n = c.n, ld = c.ld;
+        T Lc[L + 1];
+        T rinv;
+        if (CHOL) {
+            const T *Q = A.Q + c.band;
+            T a[L + 1];
+            _Pragma("unroll") for (int d = 0; d <= L; ++d) {
+                T q = (j + d < n) ? Q[(int64_t)d * ld + j] : T(0);
+                a[d] = (d < L) ? (q - pw[tri(0, d, L)]) : q;
+            }
+            T piv = a[0];
+            if (!(piv > T(0)) && out && info == 0) info = (int32_t)(j + 1);
+            rinv = Num<T>::rsq(piv);
+            Lc[0] = piv * rinv;
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) Lc[d] = a[d] * rinv;
+            if (out) {
+                T *Lo = A.L + c.band;
+                _Pragma("unroll") for (int d = 0; d <= L; ++d) Lo[(int64_t)d * ld + j] = (j + d < n) ? Lc[d] : T(0);
+                ldacc += log((double)piv);
+            }
+            // pending sums for the window of column j+1: pair (a', b') <- (a'+1, b'+1) + Lc[1+a'] Lc[1+b']
+            T npw[NT];
+            _Pragma("unroll") for (int x = 0; x < L; ++x)
+                _Pragma("unroll") for (int y = x; y < L; ++y) {
+                    T old = (y + 1 <= L - 1) ? pw[tri(x + 1, y + 1, L)] : T(0);
+                    npw[tri(x, y, L)] = fma(Lc[1 + x], Lc[1 + y], old);
+                }
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) pw[x] = npw[x];
+        } else {
+            const T *Li = A.Lin + c.band;
+            _Pragma("unroll") for (int d = 0; d <= L; ++d) Lc[d] = (j + d < n) ? Li[(int64_t)d * ld + j] : T(0);
+            rinv = Num<T>::rcp(Lc[0]);
+        }
+        if (SOLVE) {
+            const T *Bi = A.Bin + c.rhs;
+            T *Xo = A.Xout + c.rhs;
+            _Pragma("unroll") for (int r = 0; r < KK; ++r) {
+                const bool on = r < A.kk;
+                int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
+                T y = ((on ? Bi[co + j] : T(0)) - u[r][0]) * rinv;
+                if (out && on) Xo[co + j] = y;
+                _Pragma("unroll") for (int d = 0; d < L; ++d) {
+                    T old = (d + 1 < L) ? u[r][d + 1] : T(0);
+                    u[r][d] = fma(Lc[1 + d], y, old);
+                }
+            }
+        }
+        if (ALG4) {
+            const T *S = A.S + c.band;
+            const T *Sb = A.Sbar + c.band;
+            const int64_t i = j;
+            T U[L + 1], srow[L + 1], b[L + 1], bU[L + 1];
+            _Pragma("unroll") for (int t = 0; t <= L; ++t) {
+                bool in = (i + t < n);
+                U[t] = Lc[t] * rinv;
+                srow[t] = in ? S[(int64_t)t * ld + i] : T(0);
+                T sb = in ? Sb[(int64_t)t * ld + i] : T(0);
+                b[t] = (t < L ? pend[tri(0, t, L)] : T(0)) + sb;
+                bU[t] = T(0);
+            }
+            // reverse of Sym[i,i] = rinv^2 - sum_t U[t] Sym[i, i+t]
+            T bvi2 = b[0];
+            _Pragma("unroll") for (int t = 1; t <= L; ++t) {
+                bU[t] = -b[0] * srow[t];
+                b[t] = fma(-b[0], U[t], b[t]);
+            }
+            // reverse of Sym[i, i+q] = -sum_t U[t] Sigma[i+t, i+q], q = 1..L
+            T npend[NT];
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) npend[x] = T(0);
+            // carry the pending pairs that stay inside the window: (t, q) -> (t-1, q-1)
+            _Pragma("unroll") for (int t = 1; t < L; ++t)
+                _Pragma("unroll") for (int q = t; q < L; ++q) npend[tri(t - 1, q - 1, L)] = pend[tri(t, q, L)];
+            _Pragma("unroll") for (int q = 1; q <= L; ++q) {
+                _Pragma("unroll") for (int t = 1; t <= L; ++t) {
+                    bU[t] = fma(-b[q], sblk[tri(t - 1, q - 1, L)], bU[t]);
+                    npend[tri(t - 1, q - 1, L)] = fma(-b[q], U[t], npend[tri(t - 1, q - 1, L)]);
+                }
+            }
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) pend[x] = npend[x];
+            if (out) {
+                // bL = transpose(bU) / vec ; bvec = -2 bvi2 / vec^3 - sum_t bU[t] L[i+t, i] / vec^2
+                T *Lb = A.Lbar + c.band;
+                T s = T(0);
+                _Pragma("unroll") for (int t = 1; t <= L; ++t) s = fma(bU[t], Lc[t], s);
+                T r2 = rinv * rinv;
+                T bvec = T(-2) * bvi2 * r2 * rinv - s * r2;
+                T vals[L + 1];
+                vals[0] = bvec;
+                _Pragma("unroll") for (int t = 1; t <= L; ++t) vals[t] = bU[t] * rinv;
+                _Pragma("unroll") for (int t = 0; t <= L; ++t) {
+                    T *p = &Lb[(int64_t)t * ld + i];
+                    T v = (i + t < n) ? vals[t] : T(0);
+                    *p = A.acc ? (*p + v) : v;
+                }
+            }
+            // shift the Sigma block to rows/cols i+2..i+L+1
+            T nblk[NT];
+            _Pragma("unroll") for (int t = 1; t < L; ++t)
+                _Pragma("unroll") for (int q = t; q < L; ++q) nblk[tri(t - 1, q - 1, L)] = sblk[tri(t, q, L)];
+            _Pragma("unroll") for (int t = 1; t <= L; ++t) {
+                // new entries Sigma[i+1+t, i+1+L], stored at column i+1+t, diagonal L-t
+                int64_t col = i + 1 + t, row = i + 1 + L;
+                nblk[tri(t - 1, L - 1, L)] = (row < n) ? S[(int64_t)(L - t) * ld + col] : T(0);
+            }
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) sblk[x] = nblk[x];
+        }
+    }
+};
+
+// ===========================================================================
+// Register-window backward sweep: TAKA [+ SOLVE], SOLVE, ALG2 [+ SOLVE + OUTER]
+// ===========================================================================
+template <typename T, int L, int K, int FL>
+struct BwdReg {
+    static constexpr int NT = Tri<L>::N;
+    static constexpr bool TAKA = (FL & B_TAKA) != 0;
+    static constexpr bool SOLVE = (FL & B_SOLVE) != 0 && K > 0;
+    static constexpr bool ALG2 = (FL & B_ALG2) != 0;
+    static constexpr bool OUTER = (FL & B_OUTER) != 0 && SOLVE && ALG2;
+    static constexpr int KK = (SOLVE ? K : 1);
+    // computed state
+    T sblk[NT];         // TAKA: Sigma block rows/cols i+1..i+L, pair (t-1, q-1)
+    T pend[NT];         // ALG2: pending Lbar of entries (j+1+f, j-e), e in [0,L-1], f in [0, L-1-e]
+    T xw[KK][L];        // SOLVE: x_{j+1..j+L}
+    // input-derived state
+    T lwin[NT];         // ALG2: L[j+f, j-e], e in [1,L], f in [0, L-e]  -> pair (e-1, e-1+f)
+    T xin[KK][L];       // OUTER: forward X_{j+1..j+L}
+
+    static constexpr int snap_words() { return (TAKA ? NT : 0) + (ALG2 ? NT : 0) + (SOLVE ? K * L : 0); }
+
+    __device__ void save(T *dst) const {
+        int o = 0;
+        if (TAKA) { _Pragma("unroll") for (int x = 0; x < NT; ++x) dst[o++] = sblk[x]; }
+        if (ALG2) { _Pragma("unroll") for (int x = 0; x < NT; ++x) dst[o++] = pend[x]; }
+        if (SOLVE) { _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) dst[o++] = xw[r][d]; }
+    }
+    __device__ void load_state(const T *src) {
+        int o = 0;
+        if (TAKA) { _Pragma("unroll") for (int x = 0; x < NT; ++x) sblk[x] = src[o++]; }
+        if (ALG2) { _Pragma("unroll") for (int x = 0; x < NT; ++x) pend[x] = src[o++]; }
+        if (SOLVE) { _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) xw[r][d] = src[o++]; }
+    }
+    __device__ void zero() {
+        _Pragma("unroll") for (int x = 0; x < NT; ++x) { sblk[x] = T(0); pend[x] = T(0); lwin[x] = T(0); }
+        _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) { xw[r][d] = T(0); xin[r][d] = T(0); }
+    }
+
+    // Preload input-derived windows for the first iteration j0.
+    __device__ void preload(const SweepArgs<T> &A, const ChainCtx &c, int64_t j0) {
+        if (ALG2) {
+            const T *Li = A.Lin + c.band;
+            _Pragma("unroll") for (int e = 1; e <= L; ++e)
+                _Pragma("unroll") for (int f = 0; f <= L - e; ++f) {
+                    int64_t col = j0 - e, row = j0 + f;
+                    lwin[tri(e - 1, e - 1 + f, L)] = (col >= 0 && row < c.n) ? Li[(int64_t)(e + f) * c.ld + col] : T(0);
+                }
+        }
+        if (OUTER) {
+            const T *Xi = A.Xin + c.rhs;
+            _Pragma("unroll") for (int r = 0; r < KK; ++r) {
+                const bool on = r < A.kk;
+                int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
+                _Pragma("unroll") for (int d = 0; d < L; ++d) xin[r][d] = (on && j0 + 1 + d < c.n) ? Xi[co + j0 + 1 + d] : T(0);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void step(const SweepArgs<T> &A, const ChainCtx &c, int64_t j, bool out) {
+        const int64_t n = c.n, ld = c.ld;
+        const T *Li = A.Lin + c.band;
+        T Lc[L + 1];
+        if (ALG2) {
+            // the diagonal comes from the diagonal stream; the rest from the window (entries (j+d, j))
+            Lc[0] = Li[j];
+            // L[j+d, j] for d >= 1 is window entry e = ... not kept (the window holds columns < j);
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) Lc[d] = (j + d < n) ? Li[(int64_t)d * ld + j] : T(0);
+        } else {
+            _Pragma("unroll") for (int d = 0; d <= L; ++d) Lc[d] = (j + d < n) ? Li[(int64_t)d * ld + j] : T(0);
+        }
+        const T rinv = Num<T>::rcp(Lc[0]);
+        T xj[KK];
+        if (SOLVE) {
+            const T *Bi = A.Bin + c.rhs;
+            T *Xo = A.Xout + c.rhs;
+            _Pragma("unroll") for (int r = 0; r < KK; ++r) {
+                const bool on = r < A.kk;
+                int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
+                T s = on ? Bi[co + j] : T(0);
+                _Pragma("unroll") for (int d = L; d >= 1; --d) s = fma(-Lc[d], xw[r][d - 1], s);
+                xj[r] = s * rinv;
+                if (out && on) Xo[co + j] = xj[r];
+            }
+        }
+        if (TAKA) {
+            const int64_t i = j;
+            T U[L + 1], row[L + 1];
+            _Pragma("unroll") for (int t = 1; t <= L; ++t) U[t] = Lc[t] * rinv;
+            // Sym[i, i+q] = -sum_t U[t] Sigma[i+t, i+q], q = L..1 (freshest block term last)
+            _Pragma("unroll") for (int q = L; q >= 1; --q) {
+                T s = T(0);
+                _Pragma("unroll") for (int t = L; t >= 1; --t) s = fma(U[t], sblk[tri(t - 1, q - 1, L)], s);
+                row[q] = -s;
+            }
+            {
+                T s = T(0);
+                _Pragma("unroll") for (int t = L; t >= 1; --t) s = fma(U[t], row[t], s);
+                row[0] = rinv * rinv - s;
+            }
+            if (out) {
+                T *So = A.Sout + c.band;
+                _Pragma("unroll") for (int q = 0; q <= L; ++q) So[(int64_t)q * ld + i] = (i + q < n) ? row[q] : T(0);
+            }
+            // shift: new block rows/cols i..i+L-1 : (0, q) <- row[q]; (t, q) <- old (t-1, q-1)
+            T nblk[NT];
+            _Pragma("unroll") for (int q = 0; q < L; ++q) nblk[tri(0, q, L)] = (i + q < n) ? row[q] : T(0);
+            _Pragma("unroll") for (int t = 1; t < L; ++t)
+                _Pragma("unroll") for (int q = t; q < L; ++q) nblk[tri(t, q, L)] = sblk[tri(t - 1, q - 1, L)];
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) sblk[x] = nblk[x];
+        }
+        if (ALG2) {
+            const T *Lbi = A.Lbar_in + c.band;
+            T Lb[L + 1];
+            _Pragma("unroll") for (int d = 0; d <= L; ++d) {
+                T v = (j + d < n) ? Lbi[(int64_t)d * ld + j] : T(0);
+                Lb[d] = (d >= 1) ? (v + pend[tri(0, d - 1, L)]) : v;
+            }
+            if (OUTER) {
+                // Lbar -= band(X Ybar^T) + band(Bbar Y^T) with Y = L^T X, Bbar = L^{-T} Ybar
+                const T *Yb = A.Ybar + c.rhs;
+                const T *Xi = A.Xin + c.rhs;
+                _Pragma("unroll") for (int r = 0; r < KK; ++r) {
+                    const bool on = r < A.kk;
+                    int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
+                    T x0 = on ? Xi[co + j] : T(0);
+                    T ybar = on ? Yb[co + j] : T(0);
+                    T y = Lc[0] * x0;
+                    _Pragma("unroll") for (int d = 1; d <= L; ++d) y = fma(Lc[d], xin[r][d - 1], y);
+                    Lb[0] = fma(-x0, ybar, Lb[0]);
+                    Lb[0] = fma(-xj[r], y, Lb[0]);
+                    _Pragma("unroll") for (int d = 1; d <= L; ++d) {
+                        Lb[d] = fma(-xin[r][d - 1], ybar, Lb[d]);
+                        Lb[d] = fma(-xw[r][d - 1], y, Lb[d]);
+                    }
+                    // shift the X window
+                    _Pragma("unroll") for (int d = L - 1; d >= 1; --d) xin[r][d] = xin[r][d - 1];
+                    xin[r][0] = x0;
+                }
+            }
+            if (A.ldbar) Lb[0] = Lb[0] + T(2.0 * A.ldbar[c.inst]) * rinv;
+            // Alg. 2 for column j: off-diagonals first, then the diagonal
+            T Qb[L + 1];
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) {
+                Qb[d] = Lb[d] * rinv;
+                Lb[0] = fma(-Qb[d], Lc[d], Lb[0]);
+            }
+            Qb[0] = T(0.5) * Lb[0] * rinv;
+            if (out) {
+                T *Qo = A.Qbar + c.band;
+                _Pragma("unroll") for (int d = 0; d <= L; ++d) {
+                    T *p = &Qo[(int64_t)d * ld + j];
+                    T v = (j + d < n) ? Qb[d] : T(0);
+                    *p = A.acc ? (*p + v) : v;
+                }
+            }
+            // new pending for iteration j-1: entries (r, m), m = j-1-e', r = j + f', e' in [0, L-1],
+            // f' in [0, L-1-e'].  Carry: old (e, f) with e >= 1 -> (e-1, f+1).
+            T np[NT];
+            _Pragma("unroll") for (int e2 = 0; e2 < L; ++e2)
+                _Pragma("unroll") for (int f2 = 0; f2 <= L - 1 - e2; ++f2) {
+                    // old entry (e = e2 + 1, f = f2 - 1) exists when f2 >= 1 and e2 + 1 <= L - 1
+                    T old = (f2 >= 1 && e2 + 1 <= L - 1) ? pend[tri(e2 + 1, e2 + 1 + (f2 - 1), L)] : T(0);
+                    np[tri(e2, e2 + f2, L)] = old;
+                }
+            // contributions of column j: L[j+d, m] gets -Qb[d] L[j, m], L[j, m] gets -Qb[d] L[j+d, m]
+            // (d = 0: -2 Qb[0] L[j, m]) for m in [j+d-L, j-1].  m = j-1-e2, L[j+f, m] = lwin(e=e2+1, f).
+            _Pragma("unroll") for (int e2 = 0; e2 < L; ++e2) {
+                const int e = e2 + 1;
+                T ljm = lwin[tri(e - 1, e - 1, L)];            // L[j, m], f = 0
+                // d = 0
+                np[tri(e2, e2, L)] = fma(T(-2) * Qb[0], ljm, np[tri(e2, e2, L)]);
+                _Pragma("unroll") for (int d = 1; d <= L - e; ++d) {
+                    T ljdm = lwin[tri(e - 1, e - 1 + d, L)];  // L[j+d, m]
+                    np[tri(e2, e2 + d, L)] = fma(-Qb[d], ljm, np[tri(e2, e2 + d, L)]);
+                    np[tri(e2, e2, L)] = fma(-Qb[d], ljdm, np[tri(e2, e2, L)]);
+                }
+            }
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) pend[x] = np[x];
+            // shift the L window to iteration j-1: (e, f) -> (e-1, f+1) for e >= 2; new f = 0 entries
+            T nw[NT];
+            _Pragma("unroll") for (int e = 1; e <= L; ++e)
+                _Pragma("unroll") for (int f = 0; f <= L - e; ++f) {
+                    T v;
+                    if (f >= 1) v = lwin[tri(e, e + f - 1, L)];   // old (e+1, f-1), e+1 <= L since f <= L-e
+                    else {
+                        int64_t col = j - 1 - e;
+                        v = (col >= 0) ? Li[(int64_t)e * ld + col] : T(0);   // L[j-1, j-1-e]
+                    }
+                    nw[tri(e - 1, e - 1 + f, L)] = v;
+                }
+            _Pragma("unroll") for (int x = 0; x < NT; ++x) lwin[x] = nw[x];
+        }
+        if (SOLVE) {
+            _Pragma("unroll") for (int r = 0; r < KK; ++r) {
+                _Pragma("unroll") for (int d = L - 1; d >= 1; --d) xw[r][d] = xw[r][d - 1];
+                xw[r][0] = xj[r];
+            }
+        }
+    }
+};
+
+// ===========================================================================
+// Chain drivers (register windows)
+// ===========================================================================
+template <typename T, int L, int K, int FL>
+__device__ void run_fwd_reg(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, int mode,
+                            const T *exact_state) {
+    FwdReg<T, L, K, FL> s;
+    s.zero();
+    int64_t j0 = c.a;
+    if (mode == RUN_COLD && !c.first) j0 = imax64(c.a - P.warm, 0);
+    if (mode == RUN_EXACT && exact_state) s.load_state(exact_state);
+    s.preload(A, c, j0);
+    double ldacc = 0.0;
+    int32_t info = 0;
+    for (int64_t j = j0; j < c.b; ++j) {
+        if (j == c.a && !c.first && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 0));
+        s.step(A, c, j, j >= c.a, ldacc, info);
+    }
+    if (!c.last && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 1));
+    if (FL & F_CHOL) {
+        if (c.first && c.last) {
+            if (A.logdet) A.logdet[c.inst] = info ? (double)NAN : ldacc;
+            A.info[c.inst] = info;
+        } else {
+            P.seg_logdet[c.gseg] = ldacc;
+            P.seg_info[c.gseg] = info;
+        }
+    }
+}
+
+template <typename T, int L, int K, int FL>
+__device__ void run_bwd_reg(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, int mode,
+                            const T *exact_state) {
+    BwdReg<T, L, K, FL> s;
+    s.zero();
+    int64_t j0 = c.b - 1;
+    if (mode == RUN_COLD && !c.last) j0 = imin64(c.b - 1 + P.warm, c.n - 1);
+    if (mode == RUN_EXACT && exact_state) s.load_state(exact_state);
+    s.preload(A, c, j0);
+    for (int64_t j = j0; j >= c.a; --j) {
+        if (j == c.b - 1 && !c.last && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 0));
+        s.step(A, c, j, j < c.b);
+    }
+    if (!c.first && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 1));
+}
+
+// ===========================================================================
+// Generic forms for any bandwidth: one chain per instance, the windows live in
+// the outputs themselves and in two band-shaped scratch pools (zeroed before
+// the launch).  Same formulas as the register forms.
+// ===========================================================================
+template <typename T, int FL>
+__device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c) {
+    const int64_t n = c.n, ld = c.ld;
+    const int l = c.l;
+    constexpr bool CHOL = (FL & F_CHOL) != 0, ALG4 = (FL & F_ALG4) != 0;
+    const bool SOLVE = (FL & F_SOLVE) != 0 && P.k > 0;
+    const int K = SOLVE ? A.kk : 0;
+    double ldacc = 0.0;
+    int32_t info = 0;
+    T *Lw = CHOL ? A.L + c.band : nullptr;
+    const T *Lr = CHOL ? (const T *)(A.L + c.band) : A.Lin + c.band;
+#define LL(i_, j_) Lr[(int64_t)((i_) - (j_)) * ld + (j_)]
+    for (int64_t j = 0; j < n; ++j) {
+        const int dmax = (int)imin64(l, n - 1 - j);
+        T rinv;
+        if (CHOL) {
+            const T *Q = A.Q + c.band;
+            T s = T(0);
+            for (int64_t m = imax64(j - l, 0); m < j; ++m) s = fma(LL(j, m), LL(j, m), s);
+            T piv = Q[j] - s;
+            if (!(piv > T(0)) && info == 0) info = (int32_t)(j + 1);
+            T ljj = Num<T>::sqrt_(piv);
+            rinv = T(1) / ljj;
+            ldacc += log((double)piv);
+            for (int d = 1; d <= dmax; ++d) {
+                T t = T(0);
+                for (int64_t m = imax64(j + d - l, 0); m < j; ++m) t = fma(LL(j + d, m), LL(j, m), t);
+                Lw[(int64_t)d * ld + j] = (Q[(int64_t)d * ld + j] - t) * rinv;
+            }
+            Lw[j] = ljj;
+            for (int d = dmax + 1; d <= l; ++d) Lw[(int64_t)d * ld + j] = T(0);
+        } else {
+            rinv = T(1) / Lr[j];
+        }
+        if (SOLVE) {
+            const T *Bi = A.Bin + c.rhs;
+            T *Xo = A.Xout + c.rhs;
+            for (int r = 0; r < K; ++r) {
+                int64_t co = (int64_t)(A.rhs0 + r) * c.ldr;
+                T s = Bi[co + j];
+                for (int64_t m = imax64(j - l, 0); m < j; ++m) s = fma(-LL(j, m), Xo[co + m], s);
+                Xo[co + j] = s * rinv;
+            }
+        }
+        if (ALG4) {
+            // scratch : pair adjoint of the pair (i, i+q) at [q][i]
+            // scratch2: bU[i, i+t] at [t][i]
+            const T *S = A.S + c.band;
+            const T *Sb = A.Sbar + c.band;
+            T *Pp = A.scratch + c.band;
+            T *bU = A.scratch2 + c.band;
+            T *Lb = A.Lbar + c.band;
+            const int64_t i = j;
+#define SYM(a_, b_) (((a_) >= (b_)) ? S[(int64_t)((a_) - (b_)) * ld + (b_)] : S[(int64_t)((b_) - (a_)) * ld + (a_)])
+#define PAIR(a_, b_) (((a_) >= (b_)) ? Pp[(int64_t)((a_) - (b_)) * ld + (b_)] : Pp[(int64_t)((b_) - (a_)) * ld + (a_)])
+            for (int q = 0; q <= dmax; ++q) Pp[(int64_t)q * ld + i] += Sb[(int64_t)q * ld + i];
+            const T b0 = Pp[i];
+            for (int t = 1; t <= dmax; ++t) {
+                T Ut = LL(i + t, i) * rinv;
+                bU[(int64_t)t * ld + i] = -b0 * SYM(i, i + t);
+                Pp[(int64_t)t * ld + i] = fma(-b0, Ut, Pp[(int64_t)t * ld + i]);
+            }
+            for (int q = 1; q <= dmax; ++q) {
+                const T bq = Pp[(int64_t)q * ld + i];
+                for (int t = 1; t <= dmax; ++t) {
+                    T Ut = LL(i + t, i) * rinv;
+                    bU[(int64_t)t * ld + i] = fma(-bq, SYM(i + t, i + q), bU[(int64_t)t * ld + i]);
+                    T &pr = PAIR(i + t, i + q);
+                    pr = fma(-bq, Ut, pr);
+                }
+            }
+            T s = T(0);
+            for (int t = 1; t <= dmax; ++t) s = fma(bU[(int64_t)t * ld + i], LL(i + t, i), s);
+            const T r2 = rinv * rinv;
+            const T bvec = T(-2) * b0 * r2 * rinv - s * r2;
+            for (int t = 0; t <= l; ++t) {
+                T v = (t == 0) ? bvec : (t <= dmax ? bU[(int64_t)t * ld + i] * rinv : T(0));
+                T *p = &Lb[(int64_t)t * ld + i];
+                *p = A.acc ? (*p + v) : v;
+            }
+#undef SYM
+#undef PAIR
+        }
+    }
+#undef LL
+    if (CHOL) {
+        if (A.logdet) A.logdet[c.inst] = info ? (double)NAN : ldacc;
+        A.info[c.inst] = info;
+    }
+}
+
+template <typename T, int FL>
+__device__ void run_bwd_generic(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c) {
+    const int64_t n = c.n, ld = c.ld;
+    const int l = c.l;
+    constexpr bool TAKA = (FL & B_TAKA) != 0, ALG2 = (FL & B_ALG2) != 0;
+    const bool SOLVE = (FL & B_SOLVE) != 0 && P.k > 0;
+    const bool OUTER = (FL & B_OUTER) != 0 && SOLVE && ALG2;
+    const int K = SOLVE ? A.kk : 0;
+    const T *Lr = A.Lin + c.band;
+#define LL(i_, j_) Lr[(int64_t)((i_) - (j_)) * ld + (j_)]
+    for (int64_t j = n - 1; j >= 0; --j) {
+        const int dmax = (int)imin64(l, n - 1 - j);
+        const T rinv = T(1) / Lr[j];
+        if (SOLVE) {
+            const T *Bi = A.Bin + c.rhs;
+            T *Xo = A.Xout + c.rhs;
+            for (int r = 0; r < K; ++r) {
+                int64_t co = (int64_t)(A.rhs0 + r) * c.ldr;
+                T s = Bi[co + j];
+                for (int d = dmax; d >= 1; --d) s = fma(-LL(j + d, j), Xo[co + j + d], s);
+                Xo[co + j] = s * rinv;
+            }
+        }
+        if (TAKA) {
+            T *So = A.Sout + c.band;
+            const int64_t i = j;
+#define SIG(a_, b_) (((a_) >= (b_)) ? So[(int64_t)((a_) - (b_)) * ld + (b_)] : So[(int64_t)((b_) - (a_)) * ld + (a_)])
+            for (int q = dmax; q >= 1; --q) {
+                T s = T(0);
+                for (int t = dmax; t >= 1; --t) s = fma(LL(i + t, i) * rinv, SIG(i + t, i + q), s);
+                So[(int64_t)q * ld + i] = -s;
+            }
+            T s = T(0);
+            for (int t = dmax; t >= 1; --t) s = fma(LL(i + t, i) * rinv, So[(int64_t)t * ld + i], s);
+            So[i] = rinv * rinv - s;
+            for (int q = dmax + 1; q <= l; ++q) So[(int64_t)q * ld + i] = T(0);
+#undef SIG
+        }
+        if (ALG2) {
+            // scratch : pending Lbar of entry (r, m) at [r-m][m]
+            // scratch2: Lbar (then Qbar) of column j
+            T *Pp = A.scratch + c.band;
+            T *W = A.scratch2 + c.band;
+            const T *Lbi = A.Lbar_in + c.band;
+            T *Qo = A.Qbar + c.band;
+            for (int d = 0; d <= dmax; ++d) W[(int64_t)d * ld + j] = Lbi[(int64_t)d * ld + j] + (d >= 1 ? Pp[(int64_t)d * ld + j] : T(0));
+            if (OUTER) {
+                const T *Yb = A.Ybar + c.rhs;
+                const T *Xi = A.Xin + c.rhs;
+                const T *Bb = A.Xout + c.rhs;
+                for (int r = 0; r < K; ++r) {
+                    int64_t co = (int64_t)(A.rhs0 + r) * c.ldr;
+                    T y = T(0);
+                    for (int d = 0; d <= dmax; ++d) y = fma(LL(j + d, j), Xi[co + j + d], y);
+                    const T ybar = Yb[co + j];
+                    for (int d = 0; d <= dmax; ++d) {
+                        T v = W[(int64_t)d * ld + j];
+                        v = fma(-Xi[co + j + d], ybar, v);
+                        v = fma(-Bb[co + j + d], y, v);
+                        W[(int64_t)d * ld + j] = v;
+                    }
+                }
+            }
+            if (A.ldbar) W[j] = W[j] + T(2.0 * A.ldbar[c.inst]) * rinv;
+            T lb0 = W[j];
+            for (int d = 1; d <= dmax; ++d) {
+                T qb = W[(int64_t)d * ld + j] * rinv;
+                W[(int64_t)d * ld + j] = qb;
+                lb0 = fma(-qb, LL(j + d, j), lb0);
+            }
+            W[j] = T(0.5) * lb0 * rinv;
+            for (int d = 0; d <= l; ++d) {
+                T v = (d <= dmax) ? W[(int64_t)d * ld + j] : T(0);
+                T *p = &Qo[(int64_t)d * ld + j];
+                *p = A.acc ? (*p + v) : v;
+            }
+            for (int d = 0; d <= dmax; ++d) {
+                const T qb = W[(int64_t)d * ld + j];
+                for (int64_t m = imax64(j + d - l, 0); m < j; ++m) {
+                    if (d == 0) {
+                        Pp[(int64_t)(j - m) * ld + m] = fma(T(-2) * qb, LL(j, m), Pp[(int64_t)(j - m) * ld + m]);
+                    } else {
+                        Pp[(int64_t)(j + d - m) * ld + m] = fma(-qb, LL(j, m), Pp[(int64_t)(j + d - m) * ld + m]);
+                        Pp[(int64_t)(j - m) * ld + m] = fma(-qb, LL(j + d, m), Pp[(int64_t)(j - m) * ld + m]);
+                    }
+                }
+            }
+        }
+    }
+#undef LL
+}
+
+}  // namespace bnd

@@ -1,0 +1,131 @@
+"""GPU: segmentation, edge cases and failure reporting.
+
+* Splitting instances into speculative segments must not change any output:
+  after the verify/fixup pass every band and RHS output is bitwise equal to
+  the unsplit run (only the log-det, summed per segment, may differ in its
+  last bits).  A one-row warm-up forces the fixup path.
+* Degenerate shapes (n = 1, n <= l, l = 0 and bandwidths above the
+  register-window limit) agree with the oracle.
+* Undefined corners of the inputs are never read (NaN there changes nothing)
+  and are written as 0.
+* A non-SPD instance reports info = first failing row + 1 while the other
+  instances are unaffected.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_helpers import TOL, assert_close, dev, setup, sync
+from paper_1902_10078_gb300 import binding as B
+from paper_1902_10078_gb300.workloads import zero_corners
+
+pytestmark = pytest.mark.gpu
+
+LONG = [(6000, 1), (5000, 3), (7001, 7), (4500, 2), (3333, 5), (300, 4), (4096, 8)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import paper_1902_10078_gb300.build as bld
+    bld.build()
+
+
+def run_gmm(lay, plan, insts):
+    Q = dev(lay, lay.pack_band([i.Q for i in insts]))
+    Bp = dev(lay, lay.pack_rhs([i.B for i in insts]))
+    L, S, X = lay.band_pool(), lay.band_pool(), lay.rhs_pool()
+    logdet = torch.empty(lay.count, dtype=torch.float64, device="cuda")
+    info = torch.empty(lay.count, dtype=torch.int32, device="cuda")
+    B.banded_gmm_forward(plan.handle, Q, Bp, L, X, S, logdet, info)
+    Xb = dev(lay, lay.pack_rhs([i.Xbar for i in insts]))
+    Sb = dev(lay, lay.pack_band([i.Sbar for i in insts]))
+    ldb = torch.full((lay.count,), 0.5, dtype=torch.float64, device="cuda")
+    Qb, Bb = lay.band_pool(), lay.rhs_pool()
+    B.banded_gmm_backward(plan.handle, L, X, S, Xb, Sb, ldb, Qb, Bb)
+    sync()
+    return dict(L=L, S=S, X=X, Qb=Qb, Bb=Bb, logdet=logdet.cpu().numpy(), info=info.cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F32, B.BND_F64])
+@pytest.mark.parametrize("warm", [64, 1])
+def test_segmented_is_bitwise_equal_to_whole(dtype, warm):
+    insts, lay, whole = setup(LONG, 4, dtype, dict(seg_len=-1))
+    ref = run_gmm(lay, whole, insts)
+    _, _, seg = setup(LONG, 4, dtype, dict(seg_len=512, warmup=warm))
+    assert seg.chains > lay.count
+    got = run_gmm(lay, seg, insts)
+    for key in ("L", "S", "X", "Qb", "Bb"):
+        assert torch.equal(got[key], ref[key]), f"{key} differs between segmented and whole runs"
+    assert np.all(got["info"] == 0)
+    assert np.allclose(got["logdet"], ref["logdet"], rtol=1e-12, atol=0)
+    if warm == 1:
+        # a one-row warm-up cannot converge: the verify pass must have rerun segments
+        assert sum(B.bnd_plan_fixups(seg.handle, kind) for kind in range(4)) > 0
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_degenerate_shapes(dtype):
+    shapes = [(1, 1), (1, 7), (2, 5), (3, 3), (4, 0), (40, 0), (50, 12), (23, 9), (200, 16), (8, 30)]
+    insts, lay, plan = setup(shapes, 2, dtype, dict(seg_len=-1))
+    got = run_gmm(lay, plan, insts)
+    res, _ = O.batch_step(insts)
+    tol = TOL[dtype]
+    Lg, Sg, Qg = lay.unpack_band(got["L"]), lay.unpack_band(got["S"]), lay.unpack_band(got["Qb"])
+    Xg, Bg = lay.unpack_rhs(got["X"]), lay.unpack_rhs(got["Bb"])
+    for c, r in enumerate(res):
+        assert got["info"][c] == 0
+        assert_close("L", Lg[c], r["L"], tol["fwd"])
+        assert_close("S", Sg[c], r["S"], tol["fwd"])
+        assert_close("X", Xg[c], r["X"], tol["fwd"])
+        assert_close("Qbar", Qg[c], r["Qbar"], tol["grad"])
+        assert_close("Bbar", Bg[c], r["Bbar"], tol["grad"])
+        assert abs(got["logdet"][c] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F32, B.BND_F64])
+def test_corners_never_read_and_written_zero(dtype):
+    shapes = [(50, 3), (9, 7), (700, 5), (3000, 2)]
+    insts, lay, plan = setup(shapes, 1, dtype, dict(seg_len=256, warmup=64))
+    for ins in insts:
+        zero_corners(ins.Q, fill=np.nan)
+        zero_corners(ins.Sbar, fill=np.nan)
+    got = run_gmm(lay, plan, insts)
+    for ins in insts:                         # the oracle sees zeros in the corners
+        zero_corners(ins.Q)
+        zero_corners(ins.Sbar)
+    res, _ = O.batch_step(insts)
+    for key, ref_key in (("L", "L"), ("S", "S"), ("Qb", "Qbar")):
+        arrs = lay.unpack_band(got[key])
+        for c, r in enumerate(res):
+            a = arrs[c]
+            assert np.all(np.isfinite(a)), key
+            for d in range(1, a.shape[0]):
+                assert np.all(a[d, a.shape[1] - d:] == 0.0), f"{key} corner not zero"
+            assert_close(key, a, r[ref_key], TOL[dtype]["grad"])
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+@pytest.mark.parametrize("tune", [dict(seg_len=-1), dict(seg_len=128, warmup=32)])
+def test_not_spd_reports_info(dtype, tune):
+    shapes = [(600, 2), (800, 3), (500, 1)]
+    insts, lay, plan = setup(shapes, 1, dtype, tune)
+    insts[1].Q[0, 437] = -50.0          # instance 1 fails at row 437 at the latest
+    Lo, inf = O.cholesky(insts[1].Q)
+    assert inf > 0
+    Q = dev(lay, lay.pack_band([i.Q for i in insts]))
+    L = lay.band_pool()
+    logdet = torch.empty(lay.count, dtype=torch.float64, device="cuda")
+    info = torch.empty(lay.count, dtype=torch.int32, device="cuda")
+    B.banded_cholesky(plan.handle, Q, L, logdet, info)
+    sync()
+    info = info.cpu().numpy()
+    assert info[0] == 0 and info[2] == 0
+    assert info[1] == inf
+    assert np.isnan(float(logdet[1]))
+    Lg = lay.unpack_band(L)
+    good = inf - 1
+    assert_close("rows before the failure", Lg[1][:, : max(good - 3, 1)], Lo[:, : max(good - 3, 1)],
+                 TOL[dtype]["fwd"])
+    for c in (0, 2):
+        assert_close("unaffected instance", Lg[c], O.cholesky(insts[c].Q)[0], TOL[dtype]["fwd"])
