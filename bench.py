@@ -360,8 +360,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--k", type=int, default=4)
-    ap.add_argument("--seg-len", type=int, default=1024)
-    ap.add_argument("--warm", type=int, default=64)
+    ap.add_argument("--seg-len", type=int, default=2048)
+    ap.add_argument("--warm", type=int, default=0, help="warm-up rows (0: per-bandwidth default)")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--plain", type=int, default=1)
     ap.add_argument("--plain-sample", type=int, default=64)
@@ -419,7 +419,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
-                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len, "warmup_rows": args.warm,
+                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len, "warmup_rows": args.warm or "24 l + 32",
                    "chains": r["plan"].chains, "warp_tasks": r["plan"].tasks, "graph": True,
                    "l2": "inputs (~%.1f GB) exceed L2; no flush" % (r["h2d"] / 1e9),
                    "parallelism": f"instances sharded per GPU (weak), dp{world}", "segment_fixups": r["fixups"]},

@@ -82,8 +82,10 @@ typedef struct {
 typedef struct {
     int64_t seg_len;     /* rows per chain segment; long instances are split into segments
                             run in parallel (0 = default, < 0 = never split) */
-    int32_t warmup;      /* warm-up rows of a speculative segment start (0 = default) */
+    int32_t warmup;      /* warm-up rows of a speculative segment start (0 = default:
+                            24 l + 32 rows in FP32, 48 l + 64 in FP64) */
     int32_t blocks_per_sm; /* persistent-grid occupancy (0 = default) */
+    int32_t flags;       /* bit 0: never use the shared-memory staged kernels */
 } bnd_tuning;
 
 typedef struct bnd_plan bnd_plan;

@@ -42,7 +42,7 @@ class bnd_inst(C.Structure):
 
 
 class bnd_tuning(C.Structure):
-    _fields_ = [("seg_len", C.c_int64), ("warmup", C.c_int32), ("blocks_per_sm", C.c_int32)]
+    _fields_ = [("seg_len", C.c_int64), ("warmup", C.c_int32), ("blocks_per_sm", C.c_int32), ("flags", C.c_int32)]
 
 
 _lib = None
@@ -125,7 +125,7 @@ def bnd_plan_create(dtype: int, insts, k: int, tuning=None):
     tp = None
     if tuning is not None:
         tp = C.pointer(bnd_tuning(int(tuning.get("seg_len", 0)), int(tuning.get("warmup", 0)),
-                                  int(tuning.get("blocks_per_sm", 0))))
+                                  int(tuning.get("blocks_per_sm", 0)), int(tuning.get("flags", 0))))
     h = _vp()
     _check("bnd_plan_create", lib().bnd_plan_create(C.byref(h), dtype, len(insts), arr, int(k), tp))
     return h.value

@@ -175,7 +175,13 @@ bnd_status subinv_vjp_t(const bnd_plan *p, const void *L, const void *Sm, const 
     SweepArgs<T> A = blank_args<T>(p);
     A.Lin = (const T *)L; A.S = (const T *)Sm; A.Sbar = (const T *)Sbar; A.Lbar = (T *)Lbar; A.acc = acc;
     A.kind = kSweepTakaBar;
-    return ok_or(fwd<T>(p, F_ALG4, A, s));
+    // a segment rerun by the verify pass rewrites its columns; to accumulate exactly once,
+    // segmented plans write to scratch and add it afterwards
+    const bool via_tmp = acc && p->nsegs > p->count;
+    if (via_tmp) { A.Lbar = (T *)p->dev.band_tmp; A.acc = 0; }
+    BND_CUDA(fwd<T>(p, F_ALG4, A, s));
+    if (via_tmp) BND_CUDA(launch_band_add<T>(p, (const T *)p->dev.band_tmp, (T *)Lbar, s));
+    return BND_OK;
 }
 
 template <typename T>
@@ -184,7 +190,11 @@ bnd_status chol_vjp_t(const bnd_plan *p, const void *L, const void *Lbar, const 
     SweepArgs<T> A = blank_args<T>(p);
     A.Lin = (const T *)L; A.Lbar_in = (const T *)Lbar; A.Qbar = (T *)Qbar; A.acc = acc; A.ldbar = ldbar;
     A.kind = kSweepCholBar;
-    return ok_or(bwd<T>(p, B_ALG2, A, s));
+    const bool via_tmp = acc && p->nsegs > p->count;     // see subinv_vjp_t
+    if (via_tmp) { A.Qbar = (T *)p->dev.band_tmp; A.acc = 0; }
+    BND_CUDA(bwd<T>(p, B_ALG2, A, s));
+    if (via_tmp) BND_CUDA(launch_band_add<T>(p, (const T *)p->dev.band_tmp, (T *)Qbar, s));
+    return BND_OK;
 }
 
 template <typename T>

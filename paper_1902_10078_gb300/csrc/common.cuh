@@ -28,6 +28,7 @@ struct InstDev {
     int32_t nseg;      // number of row segments
     int64_t seg0;      // global id of the instance's first segment (ids are consecutive)
     int64_t seg_len;   // rows per segment (the last one may be shorter)
+    int64_t warm;      // warm-up rows of a speculative segment start
 };
 
 // A warp task: 32 consecutive entries of the chain table (all the same l).
@@ -100,6 +101,15 @@ struct bnd_plan {
     int64_t *tile_prefix;
     int64_t ntiles;
     int32_t has_generic;       // some instance runs the generic (any-bandwidth) path
+    // tasks are grouped by bandwidth class: class 0 = generic (l = 0 or l > kRegMaxL),
+    // class c = bandwidth c; class c owns tasks [class_task0[c], class_task0[c+1])
+    int32_t class_task0[bnd::kRegMaxL + 2];
+    int32_t staged_ok;         // every offset / stride allows 16-byte tiles
+    int32_t force_direct;      // tuning: never use the staged kernels
+    cudaStream_t side[bnd::kRegMaxL + 1];
+    cudaEvent_t ev_fork;
+    cudaEvent_t ev_join[bnd::kRegMaxL + 1];
+    int32_t streams_ready;
     // workspace layout (byte offsets)
     size_t off_inst, off_chains, off_tasks, off_tiles, off_counters, off_snap, off_logdet, off_info,
         off_rhs_tmp, off_rhs_tmp2, off_band_tmp, off_band_tmp2, off_band_tmp3, ws_bytes;

@@ -13,9 +13,17 @@ using namespace bnd;
 
 namespace {
 
-constexpr int64_t kDefaultSegLen = 1024;
-constexpr int32_t kDefaultWarmF32 = 64;
-constexpr int32_t kDefaultWarmF64 = 128;
+constexpr int64_t kDefaultSegLen = 2048;
+
+// Default warm-up of a speculative segment start.  The cold-started state
+// forgets its start at a rate per block of l rows, so the warm-up grows with
+// l; measured bit-exact convergence on the uneven batch needed about 16 l rows
+// in FP32 (l = 7: 64 rows fail, 128 converge); the defaults keep a margin, and
+// FP64 needs roughly twice the distance to reach its smaller rounding unit.
+int64_t default_warm(bnd_dtype dt, int l) {
+    const int64_t w = dt == BND_F32 ? 24 * (int64_t)l + 32 : 48 * (int64_t)l + 64;
+    return (w + 3) / 4 * 4;
+}
 constexpr int32_t kMaxBand = 1024;
 constexpr int32_t kMaxRhs = 64;
 
@@ -42,13 +50,16 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->count = count;
     p->k = k;
     const size_t esz = dtype == BND_F32 ? 4 : 8;
-    p->warm = dtype == BND_F32 ? kDefaultWarmF32 : kDefaultWarmF64;
+    p->warm = 0;                                      // 0: per-bandwidth default
     p->seg_len = kDefaultSegLen;
     if (tuning) {
         if (tuning->seg_len != 0) p->seg_len = tuning->seg_len;
         if (tuning->warmup > 0) p->warm = tuning->warmup;
         if (tuning->blocks_per_sm > 0) p->blocks_per_sm = tuning->blocks_per_sm;
+        p->force_direct = (tuning->flags & 1) != 0;
     }
+    const int64_t tw = 16 / (int64_t)esz;                 // elements per 16-byte tile
+    p->staged_ok = 1;
 
     std::vector<InstDev> idev((size_t)count);
     int64_t nsegs = 0;
@@ -61,8 +72,9 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         D.n = I.n; D.band = I.band; D.ld = I.ld; D.rhs = I.rhs; D.ldr = I.ldr; D.l = I.l;
         const bool reg = I.l >= 1 && I.l <= kRegMaxL;
         if (!reg) has_generic = true;
+        D.warm = p->warm > 0 ? ((int64_t)p->warm + 3) / 4 * 4 : default_warm(dtype, I.l);
         int64_t nseg = 1;
-        if (reg && p->seg_len > 0 && I.n > p->seg_len + p->warm) {
+        if (reg && p->seg_len > 0 && I.n > p->seg_len + D.warm) {
             nseg = (I.n + p->seg_len / 2) / p->seg_len;     // nearest segment count
             if (nseg < 1) nseg = 1;
         }
@@ -74,6 +86,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         D.seg0 = nsegs;
         nsegs += nseg;
         max_l = std::max(max_l, I.l);
+        if (I.band % tw || I.ld % tw || (k > 0 && (I.rhs % tw || I.ldr % tw))) p->staged_ok = 0;
         band_extent = std::max(band_extent, I.band + (int64_t)(I.l + 1) * I.ld);
         if (k > 0) rhs_extent = std::max(rhs_extent, I.rhs + (int64_t)k * I.ldr);
     }
@@ -102,16 +115,18 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         return (x.b - x.a) > (y.b - y.a);
     });
     // tasks of 32 chains with equal l
-    struct TaskTmp { std::vector<Chain> c; int32_t l; double cost; };
+    struct TaskTmp { std::vector<Chain> c; int32_t l; int32_t cls; double cost; };
+    auto class_of = [](int l) { return (l >= 1 && l <= kRegMaxL) ? l : 0; };
     std::vector<TaskTmp> tt;
     for (size_t s = 0; s < ch.size();) {
         const int32_t l = idev[(size_t)ch[s].inst].l;
         TaskTmp t;
         t.l = l;
+        t.cls = class_of(l);
         t.cost = 0;
         while (s < ch.size() && (int)t.c.size() < kWarp && idev[(size_t)ch[s].inst].l == l) {
             const Chain &c = ch[s];
-            int64_t rows = c.b - c.a + (c.seg > 0 ? p->warm : 0);
+            int64_t rows = c.b - c.a + (c.seg > 0 ? idev[(size_t)c.inst].warm : 0);
             t.cost = std::max(t.cost, (double)rows * (double)(l + 2) * (double)(l + 2));
             t.c.push_back(c);
             ++s;
@@ -119,7 +134,19 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         while ((int)t.c.size() < kWarp) { Chain pad; pad.inst = -1; pad.seg = 0; pad.a = pad.b = 0; t.c.push_back(pad); }
         tt.push_back(std::move(t));
     }
-    std::stable_sort(tt.begin(), tt.end(), [](const TaskTmp &x, const TaskTmp &y) { return x.cost > y.cost; });
+    std::stable_sort(tt.begin(), tt.end(), [](const TaskTmp &x, const TaskTmp &y) {
+        if (x.cls != y.cls) return x.cls < y.cls;
+        return x.cost > y.cost;
+    });
+    for (int c = 0; c <= kRegMaxL + 1; ++c) p->class_task0[c] = 0;
+    {
+        int32_t t = 0;
+        for (int c = 0; c <= kRegMaxL; ++c) {
+            p->class_task0[c] = t;
+            while (t < (int32_t)tt.size() && tt[(size_t)t].cls == c) ++t;
+        }
+        p->class_task0[kRegMaxL + 1] = t;
+    }
     p->ntasks = (int32_t)tt.size();
     p->nchains = (int64_t)tt.size() * kWarp;
     p->inst = (InstDev *)std::malloc(sizeof(InstDev) * std::max<size_t>(1, (size_t)count));
@@ -196,6 +223,15 @@ extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void
     d.band_tmp2 = base + p->off_band_tmp2;
     d.band_tmp3 = base + p->off_band_tmp3;
     cudaError_t e = cudaSuccess;
+    if (!p->streams_ready) {
+        for (int c = 0; c <= kRegMaxL && e == cudaSuccess; ++c) {
+            e = cudaStreamCreateWithFlags(&p->side[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[c], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return BND_ECUDA;
+        p->streams_ready = 1;
+    }
     if (p->count) e = cudaMemcpyAsync(base + p->off_inst, p->inst, sizeof(InstDev) * (size_t)p->count, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->nchains) e = cudaMemcpyAsync(base + p->off_chains, p->chains, sizeof(Chain) * (size_t)p->nchains, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->ntasks) e = cudaMemcpyAsync(base + p->off_tasks, p->tasks, sizeof(Task) * (size_t)p->ntasks, cudaMemcpyHostToDevice, s);
@@ -210,6 +246,13 @@ extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void
 
 extern "C" void bnd_plan_destroy(bnd_plan *p) {
     if (!p) return;
+    if (p->streams_ready) {
+        for (int c = 0; c <= kRegMaxL; ++c) {
+            cudaStreamDestroy(p->side[c]);
+            cudaEventDestroy(p->ev_join[c]);
+        }
+        cudaEventDestroy(p->ev_fork);
+    }
     std::free(p->inst);
     std::free(p->chains);
     std::free(p->tasks);

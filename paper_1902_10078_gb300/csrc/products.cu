@@ -109,6 +109,30 @@ __global__ void __launch_bounds__(256) matvec_kernel(PlanDev P, MatvecArgs<T> A)
     }
 }
 
+// dst += src over the lower band of every instance (corners written as 0).
+template <typename T>
+__global__ void __launch_bounds__(256) band_add_kernel(PlanDev P, const T *src, T *dst) {
+    const int64_t tile = blockIdx.x;
+    if (tile >= P.ntiles) return;
+    const int inst = find_instance(P.tile_prefix, P.count, tile);
+    const InstDev I = P.inst[inst];
+    const int64_t j = (tile - P.tile_prefix[inst]) * 256 + threadIdx.x;
+    if (j >= I.n) return;
+    for (int d = 0; d <= I.l; ++d) {
+        const int64_t o = I.band + (int64_t)d * I.ld + j;
+        dst[o] = (j + d < I.n) ? dst[o] + src[o] : T(0);
+    }
+}
+
+template <typename T>
+cudaError_t launch_band_add(const bnd_plan *p, const T *src, T *dst, cudaStream_t s) {
+    if (p->ntiles == 0) return cudaSuccess;
+    band_add_kernel<T><<<(unsigned)p->ntiles, 256, 0, s>>>(p->dev, src, dst);
+    return cudaGetLastError();
+}
+template cudaError_t launch_band_add<float>(const bnd_plan *, const float *, float *, cudaStream_t);
+template cudaError_t launch_band_add<double>(const bnd_plan *, const double *, double *, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_product(const bnd_plan *p, const ProdArgs<T> &A, cudaStream_t s) {
     if (p->ntiles == 0) return cudaSuccess;

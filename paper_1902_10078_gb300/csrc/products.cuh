@@ -35,6 +35,7 @@ struct MatvecArgs {
 template <typename T> cudaError_t launch_product(const bnd_plan *p, const ProdArgs<T> &A, cudaStream_t s);
 template <typename T> cudaError_t launch_outer(const bnd_plan *p, const OuterArgs<T> &A, cudaStream_t s);
 template <typename T> cudaError_t launch_matvec(const bnd_plan *p, const MatvecArgs<T> &A, cudaStream_t s);
+template <typename T> cudaError_t launch_band_add(const bnd_plan *p, const T *src, T *dst, cudaStream_t s);
 
 template <typename T> struct SweepArgs;
 template <typename T> cudaError_t launch_fwd(const bnd_plan *p, int fl, int K, const SweepArgs<T> &A, cudaStream_t s);

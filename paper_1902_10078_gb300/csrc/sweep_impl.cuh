@@ -32,7 +32,10 @@
 // segments from the exact end snapshot of their predecessor.
 #pragma once
 
+#include <utility>
+
 #include "common.cuh"
+#include "sweep_io.cuh"
 
 namespace bnd {
 
@@ -91,6 +94,7 @@ struct ChainCtx {
     int64_t n, band, ld, rhs, ldr;
     int64_t a, b;        // output rows [a, b)
     int64_t gseg;        // global segment id
+    int64_t warm;        // warm-up rows of a speculative start
     int32_t inst;        // instance index
     int32_t l;
     bool first, last;    // first / last segment of the instance
@@ -112,11 +116,42 @@ __device__ inline bool snap_equal(const T *x, const T *y, int64_t words) {
     return eq;
 }
 
+// Bounds guard of a step: boundary tiles check, interior tiles compile the check away.
+template <bool CHECK>
+__device__ __forceinline__ bool inb(int64_t x, int64_t n) { return !CHECK || x < n; }
+
+// Sum of log pivots: log det Q = sum_j log(piv_j) with piv_j = L_jj^2.  FP64
+// instances sum log() in double; FP32 instances use logf with a compensated
+// (Kahan) float sum, converted to double once per chain, which keeps FP64
+// arithmetic (slow on this part) off the per-row path.
+template <typename T> struct LogSum;
+template <> struct LogSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double piv) { s += log(piv); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct LogSum<float> {
+    float s = 0.0f, comp = 0.0f;
+    __device__ __forceinline__ void add(float piv) {
+        const float y = logf(piv) - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)comp; }
+};
+
 // Start modes of a chain run.
 enum : int { RUN_COLD = 0, RUN_EXACT = 1 };
 
 // ===========================================================================
 // Register-window forward sweep: CHOL [+ SOLVE], SOLVE, ALG4 [+ SOLVE]
+// Input streams:  [0, L]      Q (CHOL) or L, diagonal d, column j
+//                 RHS block   B column r, row j                      (SOLVE)
+//                 [SA, SA+L)  S diagonal d at column j+1+L-d         (ALG4: new block entries)
+//                 SL          S diagonal L at column j               (ALG4)
+//                 [SB, SB+L]  Sbar diagonal d at column j            (ALG4)
+// Output streams: [0, L] L (CHOL) or Lbar (ALG4); then the RHS block (SOLVE)
 // ===========================================================================
 template <typename T, int L, int K, int FL>
 struct FwdReg {
@@ -125,12 +160,33 @@ struct FwdReg {
     static constexpr bool SOLVE = (FL & F_SOLVE) != 0 && K > 0;
     static constexpr bool ALG4 = (FL & F_ALG4) != 0;
     static constexpr int KK = SOLVE ? K : 1;
+    static constexpr int I_RHS = L + 1;
+    static constexpr int I_SA = I_RHS + (SOLVE ? KK : 0);
+    static constexpr int I_SL = I_SA + L;
+    static constexpr int I_SB = I_SL + 1;
+    static constexpr int NIN = I_SA + (ALG4 ? 2 * L + 2 : 0);
+    static constexpr bool BAND_OUT = CHOL || ALG4;
+    static constexpr int O_RHS = BAND_OUT ? L + 1 : 0;
+    static constexpr int NOUT = O_RHS + (SOLVE ? KK : 0);
+    __host__ __device__ static constexpr StreamSpec in_spec(int s) {
+        if (s <= L) return StreamSpec{CHOL ? POOL_Q : POOL_LIN, s, 0};
+        if (SOLVE && s < I_SA) return StreamSpec{POOL_BIN, s - I_RHS, 0};
+        if (s < I_SL) return StreamSpec{POOL_S, s - I_SA, 1 + L - (s - I_SA)};
+        if (s == I_SL) return StreamSpec{POOL_S, L, 0};
+        return StreamSpec{POOL_SBAR, s - I_SB, 0};
+    }
+    __host__ __device__ static constexpr StreamSpec out_spec(int o) {
+        if (BAND_OUT && o <= L) return StreamSpec{CHOL ? POOL_LOUT : POOL_LBAR, o, 0};
+        return StreamSpec{POOL_XOUT, o - O_RHS, 0};
+    }
+
     // computed state
     T pw[NT];           // CHOL: pending Schur sums, pair (c-j, r-j) in [0, L-1]
     T pend[NT];         // ALG4: pending pair adjoints, pair (t, q) relative to i, in [0, L-1]
     T u[KK][L];         // SOLVE: pending sums for rows j..j+L-1
     // input-derived state
     T sblk[NT];         // ALG4: Sigma block of rows/cols i+1..i+L, pair (t-1, q-1)
+    T srow[L];          // ALG4: Sigma[i, i+d], d < L, carried from the previous block
 
     static constexpr int snap_words() { return (CHOL ? NT : 0) + (ALG4 ? NT : 0) + (SOLVE ? K * L : 0); }
 
@@ -148,10 +204,11 @@ struct FwdReg {
     }
     __device__ void zero() {
         _Pragma("unroll") for (int x = 0; x < NT; ++x) { pw[x] = T(0); pend[x] = T(0); sblk[x] = T(0); }
+        _Pragma("unroll") for (int d = 0; d < L; ++d) srow[d] = T(0);
         _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) u[r][d] = T(0);
     }
 
-    // Preload the ALG4 Sigma block for iteration i0: Sigma[i0+t, i0+q], 1 <= t <= q <= L.
+    // Preload the ALG4 Sigma block and row for iteration i0 (direct loads, once per chain).
     __device__ void preload(const SweepArgs<T> &A, const ChainCtx &c, int64_t i0) {
         if (!ALG4) return;
         const T *S = A.S + c.band;
@@ -160,19 +217,20 @@ struct FwdReg {
                 int64_t col = i0 + t, row = i0 + q;
                 sblk[tri(t - 1, q - 1, L)] = (row < c.n) ? S[(int64_t)(q - t) * c.ld + col] : T(0);
             }
+        _Pragma("unroll") for (int d = 0; d < L; ++d) srow[d] = (i0 + d < c.n) ? S[(int64_t)d * c.ld + i0] : T(0);
     }
 
     // One column / row step.  `out` selects whether outputs are written.
-    __device__ __forceinline__ void step(const SweepArgs<T> &A, const ChainCtx &c, int64_t j, bool out,
-                                         double &ldacc, int32_t &info) {
-        const int64_t n = c.n, ld = c.ld;
+    template <bool CHECK, class IO>
+    __device__ __forceinline__ void step(IO &io, const SweepArgs<T> &A, const ChainCtx &c, int64_t j, int tp, bool out,
+                                         LogSum<T> &ld, int32_t &info) {
+        const int64_t n = c.n;
         T Lc[L + 1];
         T rinv;
         if (CHOL) {
-            const T *Q = A.Q + c.band;
             T a[L + 1];
             _Pragma("unroll") for (int d = 0; d <= L; ++d) {
-                T q = (j + d < n) ? Q[(int64_t)d * ld + j] : T(0);
+                T q = inb<CHECK>(j + d, n) ? io.in(d, j, tp) : T(0);
                 a[d] = (d < L) ? (q - pw[tri(0, d, L)]) : q;
             }
             T piv = a[0];
@@ -181,9 +239,8 @@ struct FwdReg {
             Lc[0] = piv * rinv;
             _Pragma("unroll") for (int d = 1; d <= L; ++d) Lc[d] = a[d] * rinv;
             if (out) {
-                T *Lo = A.L + c.band;
-                _Pragma("unroll") for (int d = 0; d <= L; ++d) Lo[(int64_t)d * ld + j] = (j + d < n) ? Lc[d] : T(0);
-                ldacc += log((double)piv);
+                _Pragma("unroll") for (int d = 0; d <= L; ++d) io.out(d, j, tp, inb<CHECK>(j + d, n) ? Lc[d] : T(0));
+                ld.add(piv);
             }
             // pending sums for the window of column j+1: pair (a', b') <- (a'+1, b'+1) + Lc[1+a'] Lc[1+b']
             T npw[NT];
@@ -194,47 +251,29 @@ struct FwdReg {
                 }
             _Pragma("unroll") for (int x = 0; x < NT; ++x) pw[x] = npw[x];
         } else {
-            const T *Li = A.Lin + c.band;
-            _Pragma("unroll") for (int d = 0; d <= L; ++d) Lc[d] = (j + d < n) ? Li[(int64_t)d * ld + j] : T(0);
+            _Pragma("unroll") for (int d = 0; d <= L; ++d) Lc[d] = inb<CHECK>(j + d, n) ? io.in(d, j, tp) : T(0);
             rinv = Num<T>::rcp(Lc[0]);
         }
-        if (SOLVE) {
-            const T *Bi = A.Bin + c.rhs;
-            T *Xo = A.Xout + c.rhs;
-            _Pragma("unroll") for (int r = 0; r < KK; ++r) {
-                const bool on = r < A.kk;
-                int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
-                T y = ((on ? Bi[co + j] : T(0)) - u[r][0]) * rinv;
-                if (out && on) Xo[co + j] = y;
-                _Pragma("unroll") for (int d = 0; d < L; ++d) {
-                    T old = (d + 1 < L) ? u[r][d + 1] : T(0);
-                    u[r][d] = fma(Lc[1 + d], y, old);
-                }
-            }
-        }
         if (ALG4) {
-            const T *S = A.S + c.band;
-            const T *Sb = A.Sbar + c.band;
             const int64_t i = j;
-            T U[L + 1], srow[L + 1], b[L + 1], bU[L + 1];
+            T U[L + 1], sr[L + 1], b[L + 1], bU[L + 1];
             _Pragma("unroll") for (int t = 0; t <= L; ++t) {
-                bool in = (i + t < n);
+                const bool in = inb<CHECK>(i + t, n);
                 U[t] = Lc[t] * rinv;
-                srow[t] = in ? S[(int64_t)t * ld + i] : T(0);
-                T sb = in ? Sb[(int64_t)t * ld + i] : T(0);
+                sr[t] = (t < L) ? srow[t] : (in ? io.in(I_SL, j, tp) : T(0));
+                T sb = in ? io.in(I_SB + t, j, tp) : T(0);
                 b[t] = (t < L ? pend[tri(0, t, L)] : T(0)) + sb;
                 bU[t] = T(0);
             }
             // reverse of Sym[i,i] = rinv^2 - sum_t U[t] Sym[i, i+t]
             T bvi2 = b[0];
             _Pragma("unroll") for (int t = 1; t <= L; ++t) {
-                bU[t] = -b[0] * srow[t];
+                bU[t] = -b[0] * sr[t];
                 b[t] = fma(-b[0], U[t], b[t]);
             }
             // reverse of Sym[i, i+q] = -sum_t U[t] Sigma[i+t, i+q], q = 1..L
             T npend[NT];
             _Pragma("unroll") for (int x = 0; x < NT; ++x) npend[x] = T(0);
-            // carry the pending pairs that stay inside the window: (t, q) -> (t-1, q-1)
             _Pragma("unroll") for (int t = 1; t < L; ++t)
                 _Pragma("unroll") for (int q = t; q < L; ++q) npend[tri(t - 1, q - 1, L)] = pend[tri(t, q, L)];
             _Pragma("unroll") for (int q = 1; q <= L; ++q) {
@@ -246,36 +285,45 @@ struct FwdReg {
             _Pragma("unroll") for (int x = 0; x < NT; ++x) pend[x] = npend[x];
             if (out) {
                 // bL = transpose(bU) / vec ; bvec = -2 bvi2 / vec^3 - sum_t bU[t] L[i+t, i] / vec^2
-                T *Lb = A.Lbar + c.band;
                 T s = T(0);
                 _Pragma("unroll") for (int t = 1; t <= L; ++t) s = fma(bU[t], Lc[t], s);
                 T r2 = rinv * rinv;
-                T bvec = T(-2) * bvi2 * r2 * rinv - s * r2;
-                T vals[L + 1];
-                vals[0] = bvec;
-                _Pragma("unroll") for (int t = 1; t <= L; ++t) vals[t] = bU[t] * rinv;
-                _Pragma("unroll") for (int t = 0; t <= L; ++t) {
-                    T *p = &Lb[(int64_t)t * ld + i];
-                    T v = (i + t < n) ? vals[t] : T(0);
-                    *p = A.acc ? (*p + v) : v;
-                }
+                io.out(0, j, tp, T(-2) * bvi2 * r2 * rinv - s * r2);
+                _Pragma("unroll") for (int t = 1; t <= L; ++t) io.out(t, j, tp, inb<CHECK>(i + t, n) ? bU[t] * rinv : T(0));
             }
-            // shift the Sigma block to rows/cols i+2..i+L+1
+            // the next row comes from the block; then shift the block to rows/cols i+2..i+L+1
+            _Pragma("unroll") for (int d = 0; d < L; ++d) srow[d] = sblk[tri(0, d, L)];
             T nblk[NT];
             _Pragma("unroll") for (int t = 1; t < L; ++t)
                 _Pragma("unroll") for (int q = t; q < L; ++q) nblk[tri(t - 1, q - 1, L)] = sblk[tri(t, q, L)];
             _Pragma("unroll") for (int t = 1; t <= L; ++t) {
-                // new entries Sigma[i+1+t, i+1+L], stored at column i+1+t, diagonal L-t
-                int64_t col = i + 1 + t, row = i + 1 + L;
-                nblk[tri(t - 1, L - 1, L)] = (row < n) ? S[(int64_t)(L - t) * ld + col] : T(0);
+                // new entry Sigma[i+1+t, i+1+L]: diagonal L-t at column i+1+t (stream I_SA + L - t)
+                nblk[tri(t - 1, L - 1, L)] = inb<CHECK>(i + 1 + L, n) ? io.in(I_SA + L - t, j, tp) : T(0);
             }
             _Pragma("unroll") for (int x = 0; x < NT; ++x) sblk[x] = nblk[x];
+        }
+        if (SOLVE) {
+            _Pragma("unroll") for (int r = 0; r < KK; ++r) {
+                const bool on = r < A.kk;
+                T y = ((on ? io.in(I_RHS + r, j, tp) : T(0)) - u[r][0]) * rinv;
+                if (out) io.out(O_RHS + r, j, tp, y);
+                _Pragma("unroll") for (int d = 0; d < L; ++d) {
+                    T old = (d + 1 < L) ? u[r][d + 1] : T(0);
+                    u[r][d] = fma(Lc[1 + d], y, old);
+                }
+            }
         }
     }
 };
 
 // ===========================================================================
 // Register-window backward sweep: TAKA [+ SOLVE], SOLVE, ALG2 [+ SOLVE + OUTER]
+// Input streams:  [0, L]     L diagonal d at column j;  with ALG2: diagonal 0 at
+//                            column j and diagonal e at column j-1-e (window)
+//                 RHS block  Bin column r, row j                     (SOLVE)
+//                 [LB, LB+L] Lbar_in diagonal d at column j          (ALG2)
+//                 X block    Xin column r, row j                     (OUTER)
+// Output streams: [0, L] S (TAKA) or Qbar (ALG2); then the RHS block (SOLVE)
 // ===========================================================================
 template <typename T, int L, int K, int FL>
 struct BwdReg {
@@ -285,13 +333,33 @@ struct BwdReg {
     static constexpr bool ALG2 = (FL & B_ALG2) != 0;
     static constexpr bool OUTER = (FL & B_OUTER) != 0 && SOLVE && ALG2;
     static constexpr int KK = (SOLVE ? K : 1);
+    static constexpr int I_RHS = L + 1;
+    static constexpr int I_LB = I_RHS + (SOLVE ? KK : 0);
+    static constexpr int I_X = I_LB + (ALG2 ? L + 1 : 0);
+    static constexpr int NIN = I_X + (OUTER ? KK : 0);
+    static constexpr bool BAND_OUT = TAKA || ALG2;
+    static constexpr int O_RHS = BAND_OUT ? L + 1 : 0;
+    static constexpr int NOUT = O_RHS + (SOLVE ? KK : 0);
+    __host__ __device__ static constexpr StreamSpec in_spec(int s) {
+        if (s <= L) return StreamSpec{POOL_LIN, s, (ALG2 && s > 0) ? -(1 + s) : 0};
+        if (SOLVE && s < I_LB) return StreamSpec{POOL_BIN, s - I_RHS, 0};
+        if (ALG2 && s < I_X) return StreamSpec{POOL_LBARIN, s - I_LB, 0};
+        return StreamSpec{POOL_XIN, s - I_X, 0};
+    }
+    __host__ __device__ static constexpr StreamSpec out_spec(int o) {
+        if (BAND_OUT && o <= L) return StreamSpec{TAKA ? POOL_SOUT : POOL_QBAR, o, 0};
+        return StreamSpec{POOL_XOUT, o - O_RHS, 0};
+    }
+
     // computed state
     T sblk[NT];         // TAKA: Sigma block rows/cols i+1..i+L, pair (t-1, q-1)
     T pend[NT];         // ALG2: pending Lbar of entries (j+1+f, j-e), e in [0,L-1], f in [0, L-1-e]
     T xw[KK][L];        // SOLVE: x_{j+1..j+L}
     // input-derived state
     T lwin[NT];         // ALG2: L[j+f, j-e], e in [1,L], f in [0, L-e]  -> pair (e-1, e-1+f)
+    T lcol[L + 1];      // ALG2: L[j+d, j], d >= 1, carried from the previous window
     T xin[KK][L];       // OUTER: forward X_{j+1..j+L}
+    T two_ldbar;        // ALG2: 2 * log-det cotangent of the instance
 
     static constexpr int snap_words() { return (TAKA ? NT : 0) + (ALG2 ? NT : 0) + (SOLVE ? K * L : 0); }
 
@@ -309,11 +377,13 @@ struct BwdReg {
     }
     __device__ void zero() {
         _Pragma("unroll") for (int x = 0; x < NT; ++x) { sblk[x] = T(0); pend[x] = T(0); lwin[x] = T(0); }
+        _Pragma("unroll") for (int d = 0; d <= L; ++d) lcol[d] = T(0);
         _Pragma("unroll") for (int r = 0; r < KK; ++r) _Pragma("unroll") for (int d = 0; d < L; ++d) { xw[r][d] = T(0); xin[r][d] = T(0); }
     }
 
-    // Preload input-derived windows for the first iteration j0.
+    // Preload input-derived windows for the first iteration j0 (direct loads, once per chain).
     __device__ void preload(const SweepArgs<T> &A, const ChainCtx &c, int64_t j0) {
+        two_ldbar = A.ldbar ? T(2.0 * A.ldbar[c.inst]) : T(0);
         if (ALG2) {
             const T *Li = A.Lin + c.band;
             _Pragma("unroll") for (int e = 1; e <= L; ++e)
@@ -321,6 +391,7 @@ struct BwdReg {
                     int64_t col = j0 - e, row = j0 + f;
                     lwin[tri(e - 1, e - 1 + f, L)] = (col >= 0 && row < c.n) ? Li[(int64_t)(e + f) * c.ld + col] : T(0);
                 }
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) lcol[d] = (j0 + d < c.n) ? Li[(int64_t)d * c.ld + j0] : T(0);
         }
         if (OUTER) {
             const T *Xi = A.Xin + c.rhs;
@@ -332,30 +403,24 @@ struct BwdReg {
         }
     }
 
-    __device__ __forceinline__ void step(const SweepArgs<T> &A, const ChainCtx &c, int64_t j, bool out) {
-        const int64_t n = c.n, ld = c.ld;
-        const T *Li = A.Lin + c.band;
+    template <bool CHECK, class IO>
+    __device__ __forceinline__ void step(IO &io, const SweepArgs<T> &A, const ChainCtx &c, int64_t j, int tp, bool out) {
+        const int64_t n = c.n;
         T Lc[L + 1];
         if (ALG2) {
-            // the diagonal comes from the diagonal stream; the rest from the window (entries (j+d, j))
-            Lc[0] = Li[j];
-            // L[j+d, j] for d >= 1 is window entry e = ... not kept (the window holds columns < j);
-            _Pragma("unroll") for (int d = 1; d <= L; ++d) Lc[d] = (j + d < n) ? Li[(int64_t)d * ld + j] : T(0);
+            Lc[0] = io.in(0, j, tp);
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) Lc[d] = lcol[d];
         } else {
-            _Pragma("unroll") for (int d = 0; d <= L; ++d) Lc[d] = (j + d < n) ? Li[(int64_t)d * ld + j] : T(0);
+            _Pragma("unroll") for (int d = 0; d <= L; ++d) Lc[d] = inb<CHECK>(j + d, n) ? io.in(d, j, tp) : T(0);
         }
         const T rinv = Num<T>::rcp(Lc[0]);
         T xj[KK];
         if (SOLVE) {
-            const T *Bi = A.Bin + c.rhs;
-            T *Xo = A.Xout + c.rhs;
             _Pragma("unroll") for (int r = 0; r < KK; ++r) {
                 const bool on = r < A.kk;
-                int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
-                T s = on ? Bi[co + j] : T(0);
+                T s = on ? io.in(I_RHS + r, j, tp) : T(0);
                 _Pragma("unroll") for (int d = L; d >= 1; --d) s = fma(-Lc[d], xw[r][d - 1], s);
                 xj[r] = s * rinv;
-                if (out && on) Xo[co + j] = xj[r];
             }
         }
         if (TAKA) {
@@ -373,33 +438,26 @@ struct BwdReg {
                 _Pragma("unroll") for (int t = L; t >= 1; --t) s = fma(U[t], row[t], s);
                 row[0] = rinv * rinv - s;
             }
-            if (out) {
-                T *So = A.Sout + c.band;
-                _Pragma("unroll") for (int q = 0; q <= L; ++q) So[(int64_t)q * ld + i] = (i + q < n) ? row[q] : T(0);
-            }
+            if (out) { _Pragma("unroll") for (int q = 0; q <= L; ++q) io.out(q, j, tp, inb<CHECK>(i + q, n) ? row[q] : T(0)); }
             // shift: new block rows/cols i..i+L-1 : (0, q) <- row[q]; (t, q) <- old (t-1, q-1)
             T nblk[NT];
-            _Pragma("unroll") for (int q = 0; q < L; ++q) nblk[tri(0, q, L)] = (i + q < n) ? row[q] : T(0);
+            _Pragma("unroll") for (int q = 0; q < L; ++q) nblk[tri(0, q, L)] = inb<CHECK>(i + q, n) ? row[q] : T(0);
             _Pragma("unroll") for (int t = 1; t < L; ++t)
                 _Pragma("unroll") for (int q = t; q < L; ++q) nblk[tri(t, q, L)] = sblk[tri(t - 1, q - 1, L)];
             _Pragma("unroll") for (int x = 0; x < NT; ++x) sblk[x] = nblk[x];
         }
         if (ALG2) {
-            const T *Lbi = A.Lbar_in + c.band;
             T Lb[L + 1];
             _Pragma("unroll") for (int d = 0; d <= L; ++d) {
-                T v = (j + d < n) ? Lbi[(int64_t)d * ld + j] : T(0);
+                T v = inb<CHECK>(j + d, n) ? io.in(I_LB + d, j, tp) : T(0);
                 Lb[d] = (d >= 1) ? (v + pend[tri(0, d - 1, L)]) : v;
             }
             if (OUTER) {
                 // Lbar -= band(X Ybar^T) + band(Bbar Y^T) with Y = L^T X, Bbar = L^{-T} Ybar
-                const T *Yb = A.Ybar + c.rhs;
-                const T *Xi = A.Xin + c.rhs;
                 _Pragma("unroll") for (int r = 0; r < KK; ++r) {
                     const bool on = r < A.kk;
-                    int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
-                    T x0 = on ? Xi[co + j] : T(0);
-                    T ybar = on ? Yb[co + j] : T(0);
+                    T x0 = on ? io.in(I_X + r, j, tp) : T(0);
+                    T ybar = on ? io.in(I_RHS + r, j, tp) : T(0);
                     T y = Lc[0] * x0;
                     _Pragma("unroll") for (int d = 1; d <= L; ++d) y = fma(Lc[d], xin[r][d - 1], y);
                     Lb[0] = fma(-x0, ybar, Lb[0]);
@@ -408,12 +466,11 @@ struct BwdReg {
                         Lb[d] = fma(-xin[r][d - 1], ybar, Lb[d]);
                         Lb[d] = fma(-xw[r][d - 1], y, Lb[d]);
                     }
-                    // shift the X window
                     _Pragma("unroll") for (int d = L - 1; d >= 1; --d) xin[r][d] = xin[r][d - 1];
                     xin[r][0] = x0;
                 }
             }
-            if (A.ldbar) Lb[0] = Lb[0] + T(2.0 * A.ldbar[c.inst]) * rinv;
+            Lb[0] = fma(two_ldbar, rinv, Lb[0]);
             // Alg. 2 for column j: off-diagonals first, then the diagonal
             T Qb[L + 1];
             _Pragma("unroll") for (int d = 1; d <= L; ++d) {
@@ -421,20 +478,11 @@ struct BwdReg {
                 Lb[0] = fma(-Qb[d], Lc[d], Lb[0]);
             }
             Qb[0] = T(0.5) * Lb[0] * rinv;
-            if (out) {
-                T *Qo = A.Qbar + c.band;
-                _Pragma("unroll") for (int d = 0; d <= L; ++d) {
-                    T *p = &Qo[(int64_t)d * ld + j];
-                    T v = (j + d < n) ? Qb[d] : T(0);
-                    *p = A.acc ? (*p + v) : v;
-                }
-            }
-            // new pending for iteration j-1: entries (r, m), m = j-1-e', r = j + f', e' in [0, L-1],
-            // f' in [0, L-1-e'].  Carry: old (e, f) with e >= 1 -> (e-1, f+1).
+            if (out) { _Pragma("unroll") for (int d = 0; d <= L; ++d) io.out(d, j, tp, inb<CHECK>(j + d, n) ? Qb[d] : T(0)); }
+            // new pending for iteration j-1 (entries (j+f', j-1-e')): carry old (e, f), e >= 1 -> (e-1, f+1)
             T np[NT];
             _Pragma("unroll") for (int e2 = 0; e2 < L; ++e2)
                 _Pragma("unroll") for (int f2 = 0; f2 <= L - 1 - e2; ++f2) {
-                    // old entry (e = e2 + 1, f = f2 - 1) exists when f2 >= 1 and e2 + 1 <= L - 1
                     T old = (f2 >= 1 && e2 + 1 <= L - 1) ? pend[tri(e2 + 1, e2 + 1 + (f2 - 1), L)] : T(0);
                     np[tri(e2, e2 + f2, L)] = old;
                 }
@@ -442,31 +490,30 @@ struct BwdReg {
             // (d = 0: -2 Qb[0] L[j, m]) for m in [j+d-L, j-1].  m = j-1-e2, L[j+f, m] = lwin(e=e2+1, f).
             _Pragma("unroll") for (int e2 = 0; e2 < L; ++e2) {
                 const int e = e2 + 1;
-                T ljm = lwin[tri(e - 1, e - 1, L)];            // L[j, m], f = 0
-                // d = 0
+                T ljm = lwin[tri(e - 1, e - 1, L)];
                 np[tri(e2, e2, L)] = fma(T(-2) * Qb[0], ljm, np[tri(e2, e2, L)]);
                 _Pragma("unroll") for (int d = 1; d <= L - e; ++d) {
-                    T ljdm = lwin[tri(e - 1, e - 1 + d, L)];  // L[j+d, m]
+                    T ljdm = lwin[tri(e - 1, e - 1 + d, L)];
                     np[tri(e2, e2 + d, L)] = fma(-Qb[d], ljm, np[tri(e2, e2 + d, L)]);
                     np[tri(e2, e2, L)] = fma(-Qb[d], ljdm, np[tri(e2, e2, L)]);
                 }
             }
             _Pragma("unroll") for (int x = 0; x < NT; ++x) pend[x] = np[x];
-            // shift the L window to iteration j-1: (e, f) -> (e-1, f+1) for e >= 2; new f = 0 entries
+            // column j-1 of L (below the diagonal) is window column e = 1; then shift the window:
+            // (e, f) -> (e-1, f+1) for e >= 2, new f = 0 entries L[j-1, j-1-e] (stream e)
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) lcol[d] = lwin[tri(0, d - 1, L)];
             T nw[NT];
             _Pragma("unroll") for (int e = 1; e <= L; ++e)
                 _Pragma("unroll") for (int f = 0; f <= L - e; ++f) {
                     T v;
-                    if (f >= 1) v = lwin[tri(e, e + f - 1, L)];   // old (e+1, f-1), e+1 <= L since f <= L-e
-                    else {
-                        int64_t col = j - 1 - e;
-                        v = (col >= 0) ? Li[(int64_t)e * ld + col] : T(0);   // L[j-1, j-1-e]
-                    }
+                    if (f >= 1) v = lwin[tri(e, e + f - 1, L)];
+                    else v = io.in(e, j, tp);      // L[j-1, j-1-e] (zero when the column is < 0)
                     nw[tri(e - 1, e - 1 + f, L)] = v;
                 }
             _Pragma("unroll") for (int x = 0; x < NT; ++x) lwin[x] = nw[x];
         }
         if (SOLVE) {
+            if (out) { _Pragma("unroll") for (int r = 0; r < KK; ++r) io.out(O_RHS + r, j, tp, xj[r]); }
             _Pragma("unroll") for (int r = 0; r < KK; ++r) {
                 _Pragma("unroll") for (int d = L - 1; d >= 1; --d) xw[r][d] = xw[r][d - 1];
                 xw[r][0] = xj[r];
@@ -475,25 +522,67 @@ struct BwdReg {
     }
 };
 
+
 // ===========================================================================
-// Chain drivers (register windows)
+// Chain drivers (register windows, any IO)
 // ===========================================================================
-template <typename T, int L, int K, int FL>
+template <typename T>
+__device__ __forceinline__ ChainPtrs<T> chain_ptrs(const SweepArgs<T> &A, const ChainCtx &c) {
+    ChainPtrs<T> P;
+    P.in[POOL_Q] = A.Q ? A.Q + c.band : nullptr;
+    P.in[POOL_LIN] = A.Lin ? A.Lin + c.band : nullptr;
+    P.in[POOL_S] = A.S ? A.S + c.band : nullptr;
+    P.in[POOL_SBAR] = A.Sbar ? A.Sbar + c.band : nullptr;
+    P.in[POOL_LBARIN] = A.Lbar_in ? A.Lbar_in + c.band : nullptr;
+    P.in[POOL_BIN] = A.Bin ? A.Bin + c.rhs : nullptr;
+    P.in[POOL_XIN] = A.Xin ? A.Xin + c.rhs : nullptr;
+    P.out[POOL_LOUT - POOL_LOUT] = A.L ? A.L + c.band : nullptr;
+    P.out[POOL_LBAR - POOL_LOUT] = A.Lbar ? A.Lbar + c.band : nullptr;
+    P.out[POOL_SOUT - POOL_LOUT] = A.Sout ? A.Sout + c.band : nullptr;
+    P.out[POOL_QBAR - POOL_LOUT] = A.Qbar ? A.Qbar + c.band : nullptr;
+    P.out[POOL_XOUT - POOL_LOUT] = A.Xout ? A.Xout + c.rhs : nullptr;
+    P.ld = c.ld; P.ldr = c.ldr; P.n = c.n; P.rhs0 = A.rhs0; P.acc = A.acc; P.kk = A.kk;
+    return P;
+}
+
+template <typename T, int L, int K, int FL, class IO>
 __device__ void run_fwd_reg(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, int mode,
-                            const T *exact_state) {
-    FwdReg<T, L, K, FL> s;
+                            const T *exact_state, IO &io) {
+    using SW = FwdReg<T, L, K, FL>;
+    constexpr int TW = IO::TW;
+    SW s;
     s.zero();
     int64_t j0 = c.a;
-    if (mode == RUN_COLD && !c.first) j0 = imax64(c.a - P.warm, 0);
+    if (mode == RUN_COLD && !c.first) j0 = imax64(c.a - c.warm, 0);
     if (mode == RUN_EXACT && exact_state) s.load_state(exact_state);
     s.preload(A, c, j0);
-    double ldacc = 0.0;
+    const int64_t jend = c.b - 1;
+    const int64_t m0 = floordiv(j0, TW), m1 = floordiv(jend, TW);
+    io.begin_tiles(m0, c.a, c.b);
+    LogSum<T> ld;
     int32_t info = 0;
-    for (int64_t j = j0; j < c.b; ++j) {
-        if (j == c.a && !c.first && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 0));
-        s.step(A, c, j, j >= c.a, ldacc, info);
+    for (int64_t m = m0; m <= m1; ++m) {
+        io.tile_begin(m);
+        const int64_t jt = m * TW;
+        if (jt == c.a && !c.first) s.save(snap_ptr<T>(P, c.gseg, 0));
+        const bool has_out = jt >= c.a;
+        // interior tile: every column of the tile and every streamed column (offsets <= L + 1) is inside the matrix
+        const bool interior = jt >= j0 && jt + TW - 1 <= jend && jt + TW + 2 * L + 1 < c.n;
+        if (interior) {
+#pragma unroll
+            for (int u = 0; u < TW; ++u) s.template step<false>(io, A, c, jt + u, u, has_out, ld, info);
+        } else {
+            for (int u = 0; u < TW; ++u) {
+                const int64_t j = jt + u;
+                if (j < j0 || j > jend) continue;
+                s.template step<true>(io, A, c, j, u, has_out, ld, info);
+            }
+        }
+        io.tile_end(m, has_out);
     }
-    if (!c.last && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 1));
+    io.finish();
+    if (!c.last) s.save(snap_ptr<T>(P, c.gseg, 1));
+    const double ldacc = ld.value();
     if (FL & F_CHOL) {
         if (c.first && c.last) {
             if (A.logdet) A.logdet[c.inst] = info ? (double)NAN : ldacc;
@@ -505,20 +594,40 @@ __device__ void run_fwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
     }
 }
 
-template <typename T, int L, int K, int FL>
+template <typename T, int L, int K, int FL, class IO>
 __device__ void run_bwd_reg(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, int mode,
-                            const T *exact_state) {
-    BwdReg<T, L, K, FL> s;
+                            const T *exact_state, IO &io) {
+    using SW = BwdReg<T, L, K, FL>;
+    constexpr int TW = IO::TW;
+    SW s;
     s.zero();
     int64_t j0 = c.b - 1;
-    if (mode == RUN_COLD && !c.last) j0 = imin64(c.b - 1 + P.warm, c.n - 1);
+    if (mode == RUN_COLD && !c.last) j0 = imin64(c.b - 1 + c.warm, c.n - 1);
     if (mode == RUN_EXACT && exact_state) s.load_state(exact_state);
     s.preload(A, c, j0);
-    for (int64_t j = j0; j >= c.a; --j) {
-        if (j == c.b - 1 && !c.last && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 0));
-        s.step(A, c, j, j < c.b);
+    const int64_t m0 = floordiv(j0, TW), m1 = floordiv(c.a, TW);
+    io.begin_tiles(m0, c.a, c.b);
+    for (int64_t m = m0; m >= m1; --m) {
+        io.tile_begin(m);
+        const int64_t jt = m * TW;
+        if (jt + TW - 1 == c.b - 1 && !c.last) s.save(snap_ptr<T>(P, c.gseg, 0));
+        const bool has_out = jt < c.b;
+        // interior tile: all its columns inside [a, j0], rows below n, window columns >= 0
+        const bool interior = jt >= c.a && jt + TW - 1 <= j0 && jt + TW + L < c.n && jt - 1 - L >= 0;
+        if (interior) {
+#pragma unroll
+            for (int u = TW - 1; u >= 0; --u) s.template step<false>(io, A, c, jt + u, u, has_out);
+        } else {
+            for (int u = TW - 1; u >= 0; --u) {
+                const int64_t j = jt + u;
+                if (j < c.a || j > j0) continue;
+                s.template step<true>(io, A, c, j, u, has_out);
+            }
+        }
+        io.tile_end(m, has_out);
     }
-    if (!c.first && P.snap_words > 0) s.save(snap_ptr<T>(P, c.gseg, 1));
+    io.finish();
+    if (!c.first) s.save(snap_ptr<T>(P, c.gseg, 1));
 }
 
 // ===========================================================================
@@ -604,7 +713,7 @@ __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
             for (int t = 0; t <= l; ++t) {
                 T v = (t == 0) ? bvec : (t <= dmax ? bU[(int64_t)t * ld + i] * rinv : T(0));
                 T *p = &Lb[(int64_t)t * ld + i];
-                *p = A.acc ? (*p + v) : v;
+                *p = (t <= dmax) ? (A.acc ? (*p + v) : v) : T(0);                  // corners: 0
             }
 #undef SYM
 #undef PAIR
@@ -689,9 +798,8 @@ __device__ void run_bwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
             }
             W[j] = T(0.5) * lb0 * rinv;
             for (int d = 0; d <= l; ++d) {
-                T v = (d <= dmax) ? W[(int64_t)d * ld + j] : T(0);
                 T *p = &Qo[(int64_t)d * ld + j];
-                *p = A.acc ? (*p + v) : v;
+                *p = (d <= dmax) ? (A.acc ? (*p + W[(int64_t)d * ld + j]) : W[(int64_t)d * ld + j]) : T(0);
             }
             for (int d = 0; d <= dmax; ++d) {
                 const T qb = W[(int64_t)d * ld + j];

@@ -1,31 +1,47 @@
-// Persistent sweep kernels, the segment verify/fixup kernel and their host
-// launchers.  Included (once) by each per-dtype, per-direction translation unit.
+// Sweep kernels (staged per-bandwidth, persistent direct), the segment
+// verify/fixup kernel and their host launcher.  Included (once) by each
+// per-dtype, per-direction translation unit.
 #pragma once
+
+#include <type_traits>
 
 #include "sweep_impl.cuh"
 
 namespace bnd {
 
-// ---------------------------------------------------------------------------
-// Dispatch of one chain run on its (warp-uniform) bandwidth.
-// ---------------------------------------------------------------------------
+constexpr int kStagedWarpsPerBlock = 2;
+
+// Ring depth (16-byte tiles per stream) of the staged kernels: short
+// iterations (small l) need a deeper prefetch to cover the memory latency,
+// long ones (large l, more streams) a shallower one to fit shared memory.
+template <int L>
+struct RingDepth { static constexpr int R = L <= 4 ? 4 : 2; };
+
+template <typename T, int L, int K, int FL, bool FWD>
+struct SweepOf {
+    using type = typename std::conditional<FWD, FwdReg<T, L, K, FL>, BwdReg<T, L, K, FL>>::type;
+};
+
+template <typename T, int L, int K, int FL, bool FWD, class IO>
+__device__ __forceinline__ void run_reg(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, int mode,
+                                        const T *exact, IO &io) {
+    if constexpr (FWD) run_fwd_reg<T, L, K, FL>(P, A, c, mode, exact, io);
+    else run_bwd_reg<T, L, K, FL>(P, A, c, mode, exact, io);
+}
+
+// One chain with direct global I/O, dispatched on its bandwidth.
 template <typename T, int K, int FL, bool FWD>
-__device__ __forceinline__ void run_chain(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c,
-                                          int mode, const T *exact) {
-#define BND_CASE(LV)                                                         \
-    case LV:                                                                 \
-        if constexpr (FWD) run_fwd_reg<T, LV, K, FL>(P, A, c, mode, exact); \
-        else run_bwd_reg<T, LV, K, FL>(P, A, c, mode, exact);               \
-        break;
+__device__ __forceinline__ void run_chain_direct(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c,
+                                                 int mode, const T *exact) {
+    const ChainPtrs<T> ptrs = chain_ptrs(A, c);
+#define BND_CASE(LV)                                                                    \
+    case LV: {                                                                          \
+        DirectIO<T, typename SweepOf<T, LV, K, FL, FWD>::type> io(ptrs);               \
+        run_reg<T, LV, K, FL, FWD>(P, A, c, mode, exact, io);                          \
+        break;                                                                          \
+    }
     switch (c.l) {
-        BND_CASE(1)
-        BND_CASE(2)
-        BND_CASE(3)
-        BND_CASE(4)
-        BND_CASE(5)
-        BND_CASE(6)
-        BND_CASE(7)
-        BND_CASE(8)
+        BND_CASE(1) BND_CASE(2) BND_CASE(3) BND_CASE(4) BND_CASE(5) BND_CASE(6) BND_CASE(7) BND_CASE(8)
         default:
             if constexpr (FWD) run_fwd_generic<T, FL>(P, A, c);
             else run_bwd_generic<T, FL>(P, A, c);
@@ -37,7 +53,7 @@ __device__ __forceinline__ void run_chain(const PlanDev &P, const SweepArgs<T> &
 template <typename T, int K, int FL, bool FWD>
 __device__ __forceinline__ int state_words(int l) {
 #define BND_SW(LV) \
-    case LV: return FWD ? FwdReg<T, LV, K, FL>::snap_words() : BwdReg<T, LV, K, FL>::snap_words();
+    case LV: return SweepOf<T, LV, K, FL, FWD>::type::snap_words();
     switch (l) {
         BND_SW(1) BND_SW(2) BND_SW(3) BND_SW(4) BND_SW(5) BND_SW(6) BND_SW(7) BND_SW(8)
         default: return 0;
@@ -50,6 +66,7 @@ __device__ __forceinline__ ChainCtx make_ctx(const PlanDev &P, int32_t inst, int
     ChainCtx c;
     c.n = I.n; c.band = I.band; c.ld = I.ld; c.rhs = I.rhs; c.ldr = I.ldr; c.l = I.l;
     c.inst = inst;
+    c.warm = I.warm;
     c.gseg = I.seg0 + seg;
     c.a = (int64_t)seg * I.seg_len;
     c.b = imin64(c.a + I.seg_len, I.n);
@@ -59,23 +76,54 @@ __device__ __forceinline__ ChainCtx make_ctx(const PlanDev &P, int32_t inst, int
 }
 
 // ---------------------------------------------------------------------------
-// Persistent sweep kernel: each warp takes 32-chain tasks from a queue
-// ordered longest first; each lane runs one chain.
+// Staged kernel for one bandwidth L: block b runs warp tasks
+// [task0 + WPB b, task0 + WPB (b+1)) of the bandwidth's task range (ordered
+// longest first); each lane runs one chain through its shared-memory rings.
+// ---------------------------------------------------------------------------
+template <typename T, int L, int K, int FL, bool FWD>
+__global__ void __launch_bounds__(kWarp * kStagedWarpsPerBlock)
+staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
+    using SW = typename SweepOf<T, L, K, FL, FWD>::type;
+    using IO = StagedIO<T, SW, RingDepth<L>::R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const int t = blockIdx.x * kStagedWarpsPerBlock + warp;
+    if (t >= ntasks) return;
+    const Task task = P.tasks[task0 + t];
+    const Chain ch = P.chains[(int64_t)task.chain0 + lane];
+    if (ch.inst < 0) return;
+    const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
+    const ChainPtrs<T> ptrs = chain_ptrs(A, c);
+    T *wsm = reinterpret_cast<T *>(smem_raw) + (size_t)warp * IO::kWarpElems;
+    IO io(ptrs, wsm, lane, FWD ? 1 : -1);
+    run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
+}
+
+template <typename T, int L, int K, int FL, bool FWD>
+constexpr size_t staged_smem_bytes() {
+    using SW = typename SweepOf<T, L, K, FL, FWD>::type;
+    return sizeof(T) * (size_t)StagedIO<T, SW, RingDepth<L>::R>::kWarpElems * kStagedWarpsPerBlock;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent direct kernel: warps take 32-chain tasks of [task0, task0+ntasks)
+// from a queue; each lane runs one chain with direct global I/O.  Used for
+// bandwidths above the register-window limit and for unaligned layouts.
 // ---------------------------------------------------------------------------
 template <typename T, int K, int FL, bool FWD>
-__global__ void __launch_bounds__(128) sweep_kernel(PlanDev P, SweepArgs<T> A) {
+__global__ void __launch_bounds__(128) sweep_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
     const int lane = threadIdx.x & (kWarp - 1);
     unsigned int *head = P.counters + A.kind;
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(head, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= P.ntasks) break;
-        const Task task = P.tasks[t];
+        if (t >= ntasks) break;
+        const Task task = P.tasks[task0 + t];
         const Chain ch = P.chains[(int64_t)task.chain0 + lane];
         if (ch.inst >= 0) {
             const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
-            run_chain<T, K, FL, FWD>(P, A, c, RUN_COLD, nullptr);
+            run_chain_direct<T, K, FL, FWD>(P, A, c, RUN_COLD, nullptr);
         }
     }
 }
@@ -100,7 +148,7 @@ __global__ void __launch_bounds__(64) verify_kernel(PlanDev P, SweepArgs<T> A) {
             const int64_t g = I.seg0 + p;
             const T *prev_end = snap_ptr<T>(P, g - 1, 1);
             if (!snap_equal(prev_end, (const T *)snap_ptr<T>(P, g, 0), words)) {
-                run_chain<T, K, FL, FWD>(P, A, make_ctx(P, inst, p), RUN_EXACT, prev_end);
+                run_chain_direct<T, K, FL, FWD>(P, A, make_ctx(P, inst, p), RUN_EXACT, prev_end);
                 ++fixes;
             }
         }
@@ -109,7 +157,7 @@ __global__ void __launch_bounds__(64) verify_kernel(PlanDev P, SweepArgs<T> A) {
             const int64_t g = I.seg0 + p;
             const T *next_end = snap_ptr<T>(P, g + 1, 1);
             if (!snap_equal(next_end, (const T *)snap_ptr<T>(P, g, 0), words)) {
-                run_chain<T, K, FL, FWD>(P, A, make_ctx(P, inst, p), RUN_EXACT, next_end);
+                run_chain_direct<T, K, FL, FWD>(P, A, make_ctx(P, inst, p), RUN_EXACT, next_end);
                 ++fixes;
             }
         }
@@ -130,8 +178,35 @@ __global__ void __launch_bounds__(64) verify_kernel(PlanDev P, SweepArgs<T> A) {
 // ---------------------------------------------------------------------------
 // Host launcher
 // ---------------------------------------------------------------------------
+inline bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+inline bool args_aligned16(const SweepArgs<T> &A) {
+    return aligned16(A.Q) && aligned16(A.L) && aligned16(A.Lin) && aligned16(A.S) && aligned16(A.Sbar) &&
+           aligned16(A.Sout) && aligned16(A.Lbar) && aligned16(A.Lbar_in) && aligned16(A.Qbar) &&
+           aligned16(A.Bin) && aligned16(A.Xout) && aligned16(A.Xin) && aligned16(A.Ybar);
+}
+
+template <typename T, int L, int K, int FL, bool FWD>
+static cudaError_t launch_staged_l(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
+    const int32_t t0 = p->class_task0[L], nt = p->class_task0[L + 1] - t0;
+    if (nt <= 0) return cudaSuccess;
+    constexpr size_t smem = staged_smem_bytes<T, L, K, FL, FWD>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(staged_kernel<T, L, K, FL, FWD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const unsigned blocks = (unsigned)((nt + kStagedWarpsPerBlock - 1) / kStagedWarpsPerBlock);
+    staged_kernel<T, L, K, FL, FWD><<<blocks, kWarp * kStagedWarpsPerBlock, smem, s>>>(p->dev, A, t0, nt);
+    return cudaGetLastError();
+}
+
 template <typename T, int K, int FL, bool FWD>
-static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
+static cudaError_t launch_direct(const bnd_plan *p, const SweepArgs<T> &A, int32_t t0, int32_t nt, cudaStream_t s) {
+    if (nt <= 0) return cudaSuccess;
     static int blocks_per_sm = -1;
     static int num_sms = 0;
     if (blocks_per_sm < 0) {
@@ -142,15 +217,46 @@ static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cuda
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<T, K, FL, FWD>, 128, 0);
         blocks_per_sm = b > 0 ? b : 1;
     }
-    int bps = p->blocks_per_sm > 0 ? p->blocks_per_sm : blocks_per_sm;
+    const int bps = p->blocks_per_sm > 0 ? p->blocks_per_sm : blocks_per_sm;
     int64_t blocks = (int64_t)num_sms * bps;
-    const int64_t need = (p->ntasks + 3) / 4;          // 4 warps per block
+    const int64_t need = (nt + 3) / 4;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     cudaError_t e = cudaMemsetAsync(p->dev.counters + A.kind, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    sweep_kernel<T, K, FL, FWD><<<(unsigned)blocks, 128, 0, s>>>(p->dev, A);
-    e = cudaGetLastError();
+    sweep_kernel<T, K, FL, FWD><<<(unsigned)blocks, 128, 0, s>>>(p->dev, A, t0, nt);
+    return cudaGetLastError();
+}
+
+template <typename T, int K, int FL, bool FWD>
+static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    const bool staged = p->staged_ok && args_aligned16(A) && !p->force_direct;
+    if (!staged) {
+        e = launch_direct<T, K, FL, FWD>(p, A, 0, p->ntasks, s);
+    } else {
+        // fork: one side stream per bandwidth class, each waiting on the main stream
+        e = cudaEventRecord(p->ev_fork, s);
+        for (int c = 0; c <= kRegMaxL && e == cudaSuccess; ++c) {
+            if (p->class_task0[c + 1] - p->class_task0[c] <= 0) continue;
+            cudaStream_t side = p->side[c];
+            e = cudaStreamWaitEvent(side, p->ev_fork, 0);
+            if (e != cudaSuccess) break;
+            switch (c) {
+                case 0: e = launch_direct<T, K, FL, FWD>(p, A, p->class_task0[0], p->class_task0[1] - p->class_task0[0], side); break;
+                case 1: e = launch_staged_l<T, 1, K, FL, FWD>(p, A, side); break;
+                case 2: e = launch_staged_l<T, 2, K, FL, FWD>(p, A, side); break;
+                case 3: e = launch_staged_l<T, 3, K, FL, FWD>(p, A, side); break;
+                case 4: e = launch_staged_l<T, 4, K, FL, FWD>(p, A, side); break;
+                case 5: e = launch_staged_l<T, 5, K, FL, FWD>(p, A, side); break;
+                case 6: e = launch_staged_l<T, 6, K, FL, FWD>(p, A, side); break;
+                case 7: e = launch_staged_l<T, 7, K, FL, FWD>(p, A, side); break;
+                case 8: e = launch_staged_l<T, 8, K, FL, FWD>(p, A, side); break;
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], side);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
+        }
+    }
     if (e != cudaSuccess) return e;
     if (p->nsegs > p->count) {
         verify_kernel<T, K, FL, FWD><<<(p->count + 63) / 64, 64, 0, s>>>(p->dev, A);
@@ -158,10 +264,6 @@ static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cuda
     }
     return e;
 }
-
-}  // namespace bnd
-
-namespace bnd {
 
 // (flags, K) -> kernel instantiation.  K = 0 for sweeps without right-hand
 // sides, 1 for a single column, 4 for up to four columns (runtime kk <= 4).

@@ -18,7 +18,8 @@ from paper_1902_10078_gb300.workloads import zero_corners
 pytestmark = pytest.mark.gpu
 
 DTYPES = [B.BND_F64, B.BND_F32]
-TUNINGS = {"whole": dict(seg_len=-1), "seg": dict(seg_len=256, warmup=64)}
+TUNINGS = {"whole": dict(seg_len=-1), "seg": dict(seg_len=256, warmup=64),
+           "direct": dict(seg_len=256, warmup=64, flags=1)}
 
 
 @pytest.fixture(scope="module", autouse=True)

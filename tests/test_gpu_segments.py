@@ -48,17 +48,20 @@ def run_gmm(lay, plan, insts):
 
 
 @pytest.mark.parametrize("dtype", [B.BND_F32, B.BND_F64])
-@pytest.mark.parametrize("warm", [64, 1])
-def test_segmented_is_bitwise_equal_to_whole(dtype, warm):
-    insts, lay, whole = setup(LONG, 4, dtype, dict(seg_len=-1))
+@pytest.mark.parametrize("warm", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_segmented_is_bitwise_equal_to_whole(dtype, warm, flags):
+    # staged (flags 0) and direct (flags 1) kernels run the same arithmetic: bitwise equal to each other too
+    insts, lay, whole = setup(LONG, 4, dtype, dict(seg_len=-1, flags=1))
     ref = run_gmm(lay, whole, insts)
-    _, _, seg = setup(LONG, 4, dtype, dict(seg_len=512, warmup=warm))
+    _, _, seg = setup(LONG, 4, dtype, dict(seg_len=512, warmup=warm, flags=flags))
     assert seg.chains > lay.count
     got = run_gmm(lay, seg, insts)
     for key in ("L", "S", "X", "Qb", "Bb"):
         assert torch.equal(got[key], ref[key]), f"{key} differs between segmented and whole runs"
     assert np.all(got["info"] == 0)
-    assert np.allclose(got["logdet"], ref["logdet"], rtol=1e-12, atol=0)
+    # the log-det is summed per segment: FP32 sums (compensated) may differ in the last bits
+    assert np.allclose(got["logdet"], ref["logdet"], rtol=1e-12 if dtype == B.BND_F64 else 2e-6, atol=0)
     if warm == 1:
         # a one-row warm-up cannot converge: the verify pass must have rerun segments
         assert sum(B.bnd_plan_fixups(seg.handle, kind) for kind in range(4)) > 0
