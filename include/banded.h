@@ -218,6 +218,33 @@ bnd_status banded_product_vjp(const bnd_plan *plan, const void *A, int32_t alo, 
                               int32_t transB, const void *Cbar, int32_t clo, int32_t cup,
                               void *Abar, void *Bbar, int32_t accumulate, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free precision solve (the paper has no counterpart; it exists for
+ * callers that cannot allocate device memory at all, not even a workspace to
+ * hand over -- e.g. code inside a framework hook that forbids allocation, or a
+ * process whose device memory is reserved up front by another component).
+ *
+ *   x = (L L^T)^{-1} b   for ONE instance (order n, lower bandwidth l) and one
+ *   right-hand side; L (lower band, row stride ld >= n), b and x are DEVICE
+ *   pointers, b and x hold n elements and must not alias.
+ *
+ * No plan and no workspace: the intermediate y = L^{-1} b lives in a fixed
+ * 16 MiB device array inside the library (n <= 4,194,304 in FP32,
+ * n <= 2,097,152 in FP64; larger n returns BND_EINVAL).  Every GPU that loads
+ * the library keeps that array until the process exits.  The call allocates
+ * nothing (no cudaMalloc / cudaFree, no allocating library routine).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls on a device share that device's array, which keeps the last
+ *    call's contents (nothing in it needs to start at zero).  Calls that
+ *    overlap on the same GPU (e.g. issued on two streams) race on it: order
+ *    them on one stream.
+ *  - It runs one thread per sweep: meant for availability, not throughput.
+ * ------------------------------------------------------------------------- */
+bnd_status banded_solve_precision_noalloc(bnd_dtype dtype, int64_t n, int32_t l, const void *L, int64_t ld,
+                                          const void *b, void *x, void *stream);
+
 /* Library version string (static storage). */
 const char *bnd_version(void);
 

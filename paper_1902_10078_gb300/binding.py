@@ -26,6 +26,7 @@ EXPORTS = [
     "banded_subset_inverse", "banded_subset_inverse_vjp",
     "banded_gmm_forward", "banded_gmm_backward",
     "banded_product", "banded_outer", "banded_matvec", "banded_product_vjp",
+    "banded_solve_precision_noalloc",
     "bnd_version",
 ]
 
@@ -80,6 +81,7 @@ def lib():
         "banded_matvec": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
         "banded_product_vjp": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _i32, _i32, _i32, _vp, _i32, _i32,
                                       _vp, _vp, _i32, _vp]),
+        "banded_solve_precision_noalloc": (_i32, [_i32, C.c_int64, _i32, _vp, C.c_int64, _vp, _vp, _vp]),
         "bnd_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -220,3 +222,9 @@ def banded_product_vjp(plan, A, alo, aup, transA, B, blo, bup, transB, Cbar, clo
     _check("banded_product_vjp",
            lib().banded_product_vjp(plan, _p(A), alo, aup, int(transA), _p(B), blo, bup, int(transB), _p(Cbar), clo,
                                     cup, _p(Abar), _p(Bbar), int(accumulate), _s(stream)))
+
+
+def banded_solve_precision_noalloc(dtype: int, n: int, l: int, L, ld: int, b, x, stream=None):
+    """x = (L L^T)^{-1} b for one instance without any allocation (fixed library scratch)."""
+    _check("banded_solve_precision_noalloc",
+           lib().banded_solve_precision_noalloc(int(dtype), int(n), int(l), _p(L), int(ld), _p(b), _p(x), _s(stream)))
