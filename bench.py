@@ -275,7 +275,9 @@ def run_ours(args, rank, world, device_index):
     if args.plain and rank == 0:
         plain = run_plain(args, lay, host, torch, B, BT)
 
-    launches_per_step = 4 if plan.chains == count else 8   # sweep (+ verify) kernels per fused call x 2
+    # kernels per step: 4 sweeps x (one kernel per bandwidth class present + the verify pass when segmented)
+    classes = len(set(int(l) if 1 <= int(l) <= 8 else 0 for l in lay.ls))
+    launches_per_step = 4 * (classes + (1 if plan.chains > count else 0))
     fwd_b, bwd_b, floor_b = algorithmic_bytes(lay)
     return dict(lay=lay, plan=plan, ms=ms, ms_e2e=ms_e2e, ms_fwd=ms_fwd, ms_bwd=ms_bwd, entries=entries,
                 fwd_bytes=fwd_b, bwd_bytes=bwd_b, floor_bytes=floor_b, clocks=clk, h2d=h2d, d2h=d2h,
