@@ -170,7 +170,7 @@ def run_ours(args, rank, world, device_index):
     from paper_1902_10078_gb300 import binding as B
 
     count = args.count
-    ns, ls = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919)
+    ns, ls = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919, ls=tuple(int(x) for x in args.ls.split(",")))
     lay = BT.Layout(ns, ls, args.k, B.BND_F32)
     host = generate(lay, W.BASE_SEED + rank * count, args.workers)      # before any CUDA use
     torch.cuda.set_device(device_index)
@@ -364,6 +364,7 @@ def main():
     ap.add_argument("--k", type=int, default=4)
     ap.add_argument("--seg-len", type=int, default=2048)
     ap.add_argument("--warm", type=int, default=0, help="warm-up rows (0: per-bandwidth default)")
+    ap.add_argument("--ls", default="1,2,3,5,7", help="bandwidths drawn uniformly (profiling cases)")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--plain", type=int, default=1)
     ap.add_argument("--plain-sample", type=int, default=64)

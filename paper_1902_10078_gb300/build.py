@@ -54,6 +54,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
                     "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
+    # extra nvcc flags (tuning experiments), e.g. BND_EXTRA_NVCC_FLAGS="-DBND_STAGED_WPB=1"
+    flags += os.environ.get("BND_EXTRA_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

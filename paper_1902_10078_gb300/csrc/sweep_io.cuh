@@ -8,7 +8,7 @@
 //  DirectIO : plain global loads / stores by the calling thread (used by the
 //             verify/fixup pass, which runs one chain per thread).
 //  StagedIO : per-lane shared-memory rings.  Each lane prefetches its own
-//             chain's streams D columns ahead with 16-byte cp.async copies
+//             chain's streams R tiles ahead with 16-byte cp.async copies
 //             (one 16-byte tile = TW columns), waits with per-iteration commit
 //             groups, and collects outputs in a tile buffer written back with
 //             one 16-byte vector store per stream when a tile is complete, or
@@ -41,15 +41,23 @@ __host__ __device__ constexpr bool is_rhs_pool(int p) { return p == POOL_BIN || 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// Optional L2 prefetch size of the streaming copies (128 or 256 bytes per
+// request).  Off by default: with thousands of streams in flight the extra
+// lines crowd L2 and measured no faster.
+#ifndef BND_L2_PREFETCH
+#define BND_L2_PREFETCH 0
+#endif
+#if BND_L2_PREFETCH == 256
+#define BND_L2_HINT ".L2::256B"
+#elif BND_L2_PREFETCH == 128
+#define BND_L2_HINT ".L2::128B"
+#else
+#define BND_L2_HINT ""
+#endif
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
     const int n = valid ? 16 : 0;   // src-size 0: zero fill, nothing is read
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(n) : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(void *dst, const void *src, bool valid) {
-    const int n = valid ? BYTES : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES), "r"(n)
-                 : "memory");
+    asm volatile("cp.async.cg.shared.global" BND_L2_HINT " [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -110,77 +118,120 @@ struct DirectIO {
 
 // ---------------------------------------------------------------------------
 // StagedIO
+//
+// Ring layout (per warp): stream S owns depth(S) slots of 32 lanes x TW
+// columns; element (S, slot q, lane, u) sits at base(S) + (q 32 + lane) TW + u.
+// Slots are keyed by the ROW tile (iteration tile) they serve, modulo the
+// stream's depth.  An aligned stream (offset a multiple of TW) needs one data
+// tile per row tile.  A lagged stream (any other offset) needs two aligned data
+// tiles per row tile, m + fo and m + fo + 1 (fo = floor(off / TW)); the row
+// tile m "owns" the one that is new in the sweep direction and borrows the
+// other from the previous row tile, so lagged streams keep R + 1 slots and
+// every copy is one aligned 16-byte chunk.
 // ---------------------------------------------------------------------------
-template <typename T, class SW, int R>
+template <typename T, class SW, int R, int DIR>
 struct StagedIO {
     static constexpr int NIN = SW::NIN;
     static constexpr int NOUT = SW::NOUT;
     static constexpr int TW = 16 / (int)sizeof(T);     // columns per tile (one 16-byte chunk)
-    static constexpr int kRingElems = NIN * R * kWarp * TW;
+    static constexpr int RL = R + 1;                    // slots of a lagged stream
+
+    __host__ __device__ static constexpr int off_of(int S) { return SW::in_spec(S).off; }
+    __host__ __device__ static constexpr bool lagged(int S) { return (off_of(S) % TW) != 0; }
+    __host__ __device__ static constexpr int depth(int S) { return lagged(S) ? RL : R; }
+    __host__ __device__ static constexpr int fo_of(int S) {      // floor(off / TW)
+        return off_of(S) >= 0 ? off_of(S) / TW : -((-off_of(S) + TW - 1) / TW);
+    }
+    __host__ __device__ static constexpr int rem_of(int S) { return off_of(S) - fo_of(S) * TW; }
+    __host__ __device__ static constexpr int base(int S) {
+        int b = 0;
+        for (int x = 0; x < S; ++x) b += depth(x) * kWarp * TW;
+        return b;
+    }
+    static constexpr int kRingElems = base(NIN);
     static constexpr int kOutElems = (NOUT > 0 ? NOUT : 1) * kWarp * TW;
     static constexpr int kWarpElems = kRingElems + kOutElems;
 
     const ChainPtrs<T> &P;
-    T *ring;        // this lane's ring: element (s, slot, u) at ring[((s R + slot) 32) TW + u]
+    T *ring;        // this lane's ring (lane offset applied)
     T *outb;        // this lane's out tile: element (o, u) at outb[o 32 TW + u]
-    int dir;        // +1 forward, -1 backward
     int64_t a, b;   // output columns [a, b)
-    int slot;       // ring slot of the current tile
-    T *cur;         // ring + slot offset of the current tile
+    // slots (mod R, mod R + 1) of the current row tile and of the next row tile to issue
+    int cR, cL, iR, iL;
+    const T *curR, *curLo, *curHi;   // current aligned slot; lagged low / high data tiles
 
-    __device__ StagedIO(const ChainPtrs<T> &p, T *warp_smem, int lane, int dir_)
-        : P(p), ring(warp_smem + lane * TW), outb(warp_smem + kRingElems + lane * TW), dir(dir_) {}
+    __device__ StagedIO(const ChainPtrs<T> &p, T *warp_smem, int lane)
+        : P(p), ring(warp_smem + lane * TW), outb(warp_smem + kRingElems + lane * TW) {}
 
-    // Copy the tile of stream S that holds the values of iterations [m TW, m TW + TW) into slot q:
-    // columns m TW + off .. +TW-1.  Streams whose offset is a multiple of TW move as one 16-byte
-    // chunk; the others element by element.  Columns outside [0, n) are zero filled, not read.
-    __device__ __forceinline__ void issue(int S, int64_t m, int q) {
-        const StreamSpec s = SW::in_spec(S);
-        T *dst = ring + (S * R + q) * kWarp * TW;
-        const int64_t c0 = m * TW + s.off;
-        const T *row = P.in_row(s);
-        const bool act = P.active(s);
-        if ((s.off % TW) == 0) {
-            const bool valid = act && c0 >= 0 && c0 < P.n;
-            cp_async16(dst, valid ? row + c0 : P.in[s.pool], valid);
-        } else {
-#pragma unroll
-            for (int u = 0; u < TW; ++u) {
-                const int64_t c = c0 + u;
-                const bool valid = act && c >= 0 && c < P.n;
-                cp_async_small<sizeof(T)>(dst + u, valid ? row + c : P.in[s.pool], valid);
-            }
-        }
+    __device__ static __forceinline__ int wrap_add(int x, int d, int mod) {
+        x += d;
+        return x >= mod ? x - mod : (x < 0 ? x + mod : x);
     }
 
-    __device__ __forceinline__ int slot_of(int64_t m) const { return (int)(((m % R) + R) % R); }
+    // Copy into slot q the data tile that stream S needs for row tile m (for a
+    // lagged stream: the tile row tile m owns).  Columns outside [0, n) are
+    // zero filled, not read; a chunk that starts inside [0, n) is copied whole
+    // (the tail past n lies in the row padding, ld >= n rounded up to TW, and
+    // the sweeps mask those columns).
+    __device__ __forceinline__ void issue(int S, int64_t m, int q) {
+        const StreamSpec s = SW::in_spec(S);
+        const int64_t c0 = lagged(S) ? (m + fo_of(S) + (DIR > 0 ? 1 : 0)) * TW : m * TW + s.off;
+        T *dst = ring + base(S) + q * kWarp * TW;
+        const bool valid = P.active(s) && c0 >= 0 && c0 < P.n;
+        cp_async16(dst, valid ? P.in_row(s) + c0 : P.in[s.pool], valid);
+    }
+    __device__ __forceinline__ void issue_all(int64_t m, int qR, int qL) {
+#pragma unroll
+        for (int S = 0; S < NIN; ++S) issue(S, m, lagged(S) ? qL : qR);
+    }
 
-    // Chain start: tiles m0, m0 + dir, ..., m0 + dir (R-2) are issued (one commit group each).
+    // Chain start: row tiles m0, m0 + DIR, ..., m0 + DIR (R-2) are issued (one
+    // commit group each); the first group also holds the lagged streams' tiles
+    // owned by row tile m0 - DIR.
     __device__ void begin_tiles(int64_t m0, int64_t a_, int64_t b_) {
         a = a_;
         b = b_;
-        for (int t = 0; t < R - 1; ++t) {
-            const int64_t m = m0 + dir * t;
+        cR = (int)(((m0 % R) + R) % R);
+        cL = (int)(((m0 % RL) + RL) % RL);
+        const int pL = wrap_add(cL, -DIR, RL);
 #pragma unroll
-            for (int S = 0; S < NIN; ++S) issue(S, m, slot_of(m));
+        for (int S = 0; S < NIN; ++S)
+            if (lagged(S)) issue(S, m0 - DIR, pL);
+        iR = cR;
+        iL = cL;
+        for (int t = 0; t < R - 1; ++t) {
+            issue_all(m0 + DIR * t, iR, iL);
             cp_async_commit();
+            iR = wrap_add(iR, DIR, R);
+            iL = wrap_add(iL, DIR, RL);
         }
     }
 
-    // Tile m: issue tile m + dir (R-1), then wait until tile m has landed.
+    // Row tile m (= m0 + DIR t for the t-th call): issue row tile m + DIR (R-1),
+    // then wait until row tile m has landed.
     __device__ __forceinline__ void tile_begin(int64_t m) {
-        const int64_t mn = m + dir * (R - 1);
-        const int qn = slot_of(mn);
-#pragma unroll
-        for (int S = 0; S < NIN; ++S) issue(S, mn, qn);
+        issue_all(m + DIR * (R - 1), iR, iL);
         cp_async_commit();
+        iR = wrap_add(iR, DIR, R);
+        iL = wrap_add(iL, DIR, RL);
         cp_async_wait<R - 1>();
-        slot = slot_of(m);
-        cur = ring + slot * kWarp * TW;
+        curR = ring + cR * kWarp * TW;
+        const T *own = ring + cL * kWarp * TW;
+        const T *prev = ring + wrap_add(cL, -DIR, RL) * kWarp * TW;
+        curLo = DIR > 0 ? prev : own;
+        curHi = DIR > 0 ? own : prev;
+        cR = wrap_add(cR, DIR, R);
+        cL = wrap_add(cL, DIR, RL);
     }
 
     // Value of stream S at iteration j, position u = j mod TW inside the current tile.
-    __device__ __forceinline__ T in(int S, int64_t, int u) const { return cur[S * R * kWarp * TW + u]; }
+    __device__ __forceinline__ T in(int S, int64_t, int u) const {
+        if (lagged(S)) {
+            const int p = u + rem_of(S);
+            return p < TW ? curLo[base(S) + p] : curHi[base(S) + p - TW];
+        }
+        return curR[base(S) + u];
+    }
 
     __device__ __forceinline__ void out(int O, int64_t, int u, T v) { outb[O * kWarp * TW + u] = v; }
 

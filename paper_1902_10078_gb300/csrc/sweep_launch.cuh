@@ -9,13 +9,22 @@
 
 namespace bnd {
 
-constexpr int kStagedWarpsPerBlock = 2;
+#ifndef BND_STAGED_WPB
+#define BND_STAGED_WPB 2
+#endif
+#ifndef BND_RING_SMALL_L
+#define BND_RING_SMALL_L 4
+#endif
+#ifndef BND_RING_LARGE_L
+#define BND_RING_LARGE_L 2
+#endif
+constexpr int kStagedWarpsPerBlock = BND_STAGED_WPB;
 
-// Ring depth (16-byte tiles per stream) of the staged kernels: short
-// iterations (small l) need a deeper prefetch to cover the memory latency,
-// long ones (large l, more streams) a shallower one to fit shared memory.
+// Ring depth (tiles per stream) of the staged kernels: short iterations
+// (small l) want a deeper prefetch to cover the memory latency, long ones
+// (large l, more streams) a shallower one to fit shared memory.
 template <int L>
-struct RingDepth { static constexpr int R = L <= 4 ? 4 : 2; };
+struct RingDepth { static constexpr int R = L <= 4 ? BND_RING_SMALL_L : BND_RING_LARGE_L; };
 
 template <typename T, int L, int K, int FL, bool FWD>
 struct SweepOf {
@@ -84,7 +93,7 @@ template <typename T, int L, int K, int FL, bool FWD>
 __global__ void __launch_bounds__(kWarp * kStagedWarpsPerBlock)
 staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
     using SW = typename SweepOf<T, L, K, FL, FWD>::type;
-    using IO = StagedIO<T, SW, RingDepth<L>::R>;
+    using IO = StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     const int t = blockIdx.x * kStagedWarpsPerBlock + warp;
@@ -95,14 +104,14 @@ staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
     const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
     const ChainPtrs<T> ptrs = chain_ptrs(A, c);
     T *wsm = reinterpret_cast<T *>(smem_raw) + (size_t)warp * IO::kWarpElems;
-    IO io(ptrs, wsm, lane, FWD ? 1 : -1);
+    IO io(ptrs, wsm, lane);
     run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
 }
 
 template <typename T, int L, int K, int FL, bool FWD>
 constexpr size_t staged_smem_bytes() {
     using SW = typename SweepOf<T, L, K, FL, FWD>::type;
-    return sizeof(T) * (size_t)StagedIO<T, SW, RingDepth<L>::R>::kWarpElems * kStagedWarpsPerBlock;
+    return sizeof(T) * (size_t)StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>::kWarpElems * kStagedWarpsPerBlock;
 }
 
 // ---------------------------------------------------------------------------
