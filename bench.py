@@ -35,50 +35,45 @@ from paper_1902_10078_gb300 import workloads as W  # noqa: E402
 
 METRIC = "band entries/s fwd+bwd (chol/solve/subinv), batched vs plain; % of HBM roofline"
 UNIT = "entries/s"
+LAYOUT_NOTE = {
+    "panels": "lower-band storage (l+1) x n per instance, 32 instances of equal l interleaved per column "
+              "(column stride 32); instances ordered by (l, n)",
+    "rows": "lower-band storage (l+1) x n per instance, each diagonal contiguous (column stride 1)",
+}
 WORKLOAD = "uneven batch: 4096 instances, n log-uniform [1000, 65536], l in {1,2,3,5,7}, k=4 RHS, FP32"
 
 
 # --------------------------------------------------------------------------- inputs
 
 def _fill_worker(args):
-    """Generate instances [i0, i1); return their contiguous slices of the pools."""
-    i0, i1, seed, lay_state = args
-    from paper_1902_10078_gb300.batch import Layout
-    lay = Layout.__new__(Layout)
-    lay.__dict__.update(lay_state)
-    b0 = lay.band_off[i0]
-    b1 = lay.band_off[i1] if i1 < lay.count else lay.band_elems
-    r0 = lay.rhs_off[i0]
-    r1 = lay.rhs_off[i1] if i1 < lay.count else lay.rhs_elems
-    out = {"Q": np.zeros(b1 - b0, np.float32), "Sbar": np.zeros(b1 - b0, np.float32),
-           "B": np.zeros(r1 - r0, np.float32), "Xbar": np.zeros(r1 - r0, np.float32)}
+    """Generate instances [i0, i1); return their band / RHS arrays."""
+    i0, i1, seed, ns, ls, k = args
+    out = []
     for i in range(i0, i1):
-        ins = W.make_instance(lay.ns[i], lay.ls[i], lay.k, seed + i)
-        o, ld, rows = lay.band_off[i] - b0, lay.ld[i], lay.rows[i]
-        for key, a in (("Q", ins.Q), ("Sbar", ins.Sbar)):
-            out[key][o:o + rows * ld].reshape(rows, ld)[: a.shape[0], : lay.ns[i]] = a
-        o = lay.rhs_off[i] - r0
-        for key, a in (("B", ins.B), ("Xbar", ins.Xbar)):
-            out[key][o:o + lay.k * ld].reshape(lay.k, ld)[:, : lay.ns[i]] = a
-    return (b0, b1, r0, r1), out
+        ins = W.make_instance(ns[i], ls[i], k, seed + i)
+        out.append((i, ins.Q.astype(np.float32), ins.Sbar.astype(np.float32), ins.B.astype(np.float32),
+                    ins.Xbar.astype(np.float32)))
+    return out
 
 
 def generate(lay, seed, workers):
-    """Host pools Q, Sbar (band) and B, Xbar (RHS), generated by a spawn pool
-    (started before any CUDA use) over contiguous chunks of instances."""
+    """Host pools Q, Sbar (band) and B, Xbar (RHS) in the layout's arrangement,
+    generated by a spawn pool (started before any CUDA use) over chunks of
+    instances and packed through the layout's per-instance views."""
     import multiprocessing as mp
     pools = {"Q": np.zeros(lay.band_elems, np.float32), "Sbar": np.zeros(lay.band_elems, np.float32),
              "B": np.zeros(lay.rhs_elems, np.float32), "Xbar": np.zeros(lay.rhs_elems, np.float32)}
     chunks = max(1, min(workers * 4, lay.count))
     bounds = np.linspace(0, lay.count, chunks + 1).astype(int)
-    jobs = [(int(bounds[c]), int(bounds[c + 1]), seed, lay.__dict__) for c in range(chunks) if bounds[c + 1] > bounds[c]]
+    jobs = [(int(bounds[c]), int(bounds[c + 1]), seed, lay.ns, lay.ls, lay.k)
+            for c in range(chunks) if bounds[c + 1] > bounds[c]]
 
     def put(res):
-        (b0, b1, r0, r1), out = res
-        pools["Q"][b0:b1] = out["Q"]
-        pools["Sbar"][b0:b1] = out["Sbar"]
-        pools["B"][r0:r1] = out["B"]
-        pools["Xbar"][r0:r1] = out["Xbar"]
+        for i, q, sb, b, xb in res:
+            lay.band_view(pools["Q"], i)[: q.shape[0]] = q
+            lay.band_view(pools["Sbar"], i)[: sb.shape[0]] = sb
+            lay.rhs_view(pools["B"], i)[: b.shape[0]] = b
+            lay.rhs_view(pools["Xbar"], i)[: xb.shape[0]] = xb
     if workers > 1:
         with mp.get_context("spawn").Pool(workers) as pool:
             for res in pool.imap_unordered(_fill_worker, jobs):
@@ -171,13 +166,19 @@ def run_ours(args, rank, world, device_index):
 
     count = args.count
     ns, ls = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919, ls=tuple(int(x) for x in args.ls.split(",")))
-    lay = BT.Layout(ns, ls, args.k, B.BND_F32)
+    panels = args.layout == "panels"
+    if panels:       # the same instances, ordered so that panel groups are full and even
+        order = BT.panel_order(ns, ls)
+        ns, ls = [ns[i] for i in order], [ls[i] for i in order]
+    lay = BT.Layout(ns, ls, args.k, B.BND_F32, panels=panels)
     host = generate(lay, W.BASE_SEED + rank * count, args.workers)      # before any CUDA use
     torch.cuda.set_device(device_index)
     from paper_1902_10078_gb300 import build as bld
     bld.build()
     tuning = dict(seg_len=args.seg_len, warmup=args.warm)
     plan = BT.Plan(lay, tuning)
+    expect = B.LAYOUT_PANELS if panels else B.LAYOUT_ROWS
+    assert B.bnd_plan_layout(plan.handle) == expect, "the plan did not take the intended arrangement"
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     L, S, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool()
     X, Bb = lay.rhs_pool(), lay.rhs_pool()
@@ -296,12 +297,10 @@ def run_plain(args, lay, host, torch, B, BT):
         plan = BT.Plan(sub, dict(seg_len=args.seg_len, warmup=args.warm))
 
         def cut_band(key):
-            o, ld, rows = lay.band_off[i], lay.ld[i], lay.rows[i]
-            return torch.from_numpy(host[key][o:o + rows * ld].copy()).cuda()
+            return torch.from_numpy(sub.pack_band([lay.band_view(host[key], i)])).cuda()
 
         def cut_rhs(key):
-            o, ld = lay.rhs_off[i], lay.ld[i]
-            return torch.from_numpy(host[key][o:o + lay.k * ld].copy()).cuda()
+            return torch.from_numpy(sub.pack_rhs([lay.rhs_view(host[key], i)])).cuda()
         Q, Sb, Bm, Xb = cut_band("Q"), cut_band("Sbar"), cut_rhs("B"), cut_rhs("Xbar")
         L, S, Qb = torch.empty_like(Q), torch.empty_like(Q), torch.empty_like(Q)
         X, Bb = torch.empty_like(Bm), torch.empty_like(Bm)
@@ -365,6 +364,8 @@ def main():
     ap.add_argument("--seg-len", type=int, default=2048)
     ap.add_argument("--warm", type=int, default=0, help="warm-up rows (0: per-bandwidth default)")
     ap.add_argument("--ls", default="1,2,3,5,7", help="bandwidths drawn uniformly (profiling cases)")
+    ap.add_argument("--layout", default="panels", choices=["panels", "rows"],
+                    help="pool arrangement: 32-instance panels (cs = 32) or one contiguous row per diagonal")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--plain", type=int, default=1)
     ap.add_argument("--plain-sample", type=int, default=64)
@@ -421,7 +422,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
+        "config": {"workload": WORKLOAD, "layout": LAYOUT_NOTE[args.layout],
+                   "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
                    "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len, "warmup_rows": args.warm or "24 l + 32",
                    "chains": r["plan"].chains, "warp_tasks": r["plan"].tasks, "graph": True,
                    "l2": "inputs (~%.1f GB) exceed L2; no flush" % (r["h2d"] / 1e9),

@@ -13,15 +13,37 @@
  * reading of the paper's index formula).  Lower-banded operands (L, and the
  * symmetric Q, S, Qbar, Sbar stored by their lower half) use up = 0:
  *     B'[d][j] = B[j + d, j],   d = 0..l.
- * Row d of B' is contiguous: element (d, j) of instance i lives at
- *     pool[inst[i].band + d * inst[i].ld + j].
+ * Element (d, j) of instance i lives at
+ *     pool[inst[i].band + d * inst[i].ld + j * cs_i],   cs_i = inst[i].cs (0 means 1).
  * Corner entries (j + d >= n for lower bands) are never read; outputs write 0
  * there.  Every band operand of one call uses the same per-instance offset
- * `band` and row stride `ld`; the caller sizes each instance's region for the
- * tallest operand of the call (e.g. lo+up+1 rows for products).
+ * `band`, row stride `ld` and column stride `cs`; the caller sizes each
+ * instance's region for the tallest operand of the call (e.g. lo+up+1 rows
+ * for products).
  *
  * Right-hand sides are n x k column blocks: element (j, r) of instance i at
- *     pool[inst[i].rhs + r * inst[i].ldr + j].
+ *     pool[inst[i].rhs + r * inst[i].ldr + j * cs_i].
+ *
+ * Two arrangements of a batch in a pool have fast paths:
+ *  - rows (cs = 1): each row of B' (and each RHS column) is contiguous.  The
+ *    sweeps stage every instance's rows through shared memory lane by lane.
+ *    Offsets band, rhs and strides ld, ldr that are multiples of 16 bytes
+ *    keep the staged kernels; other values run the direct kernels.
+ *  - panels (cs = 32): instances come in groups.  A group is a run of at
+ *    most 32 consecutive descriptors whose offsets step by one -- the p-th
+ *    descriptor of the run ("lane" p) has band = band_g + p and
+ *    rhs = rhs_g + p -- and which share l, ld and ldr; ld and ldr are
+ *    multiples of 32 and band_g, rhs_g multiples of 16 bytes.  A descriptor
+ *    that does not continue the previous run starts a new group.  Row d,
+ *    column j of the 32 lanes are then 32 adjacent elements, so one warp
+ *    moves whole 128-byte (FP32) lines: this is the layout that reaches HBM
+ *    bandwidth.  The kernels read all 32 lanes of a group row even where a
+ *    lane is absent or shorter, so each group's pool region must span
+ *    (rows) x ld elements from band_g (k x ldr from rhs_g).  Descriptors
+ *    should be ordered so that a group's orders n are close (e.g. sorted)
+ *    and groups are full; a group advances at the pace of its longest
+ *    member.
+ * Any other column stride is accepted and runs the direct kernels.
  *
  * Symmetric matrices (Q, S = band(Q^{-1})) are stored by their lower band;
  * their gradients (Qbar, Sbar) are gradients with respect to these STORED
@@ -71,11 +93,12 @@ typedef enum { BND_F32 = 0, BND_F64 = 1 } bnd_dtype;
 typedef struct {
     int64_t n;      /* order of the matrix, n >= 1 */
     int64_t band;   /* element offset of B'[0][0] in every band pool of a call */
-    int64_t ld;     /* row stride of B' in elements, ld >= n */
+    int64_t ld;     /* row stride of B' in elements, ld >= n * cs */
     int64_t rhs;    /* element offset of the first RHS column in every RHS pool */
-    int64_t ldr;    /* column stride of the RHS block in elements, ldr >= n (ignored if k = 0) */
+    int64_t ldr;    /* stride between RHS columns in elements, ldr >= n * cs (ignored if k = 0) */
     int32_t l;      /* lower bandwidth, 0 <= l <= 1024 */
-    int32_t reserved;
+    int32_t cs;     /* column stride in elements of the band and the RHS block
+                       (0 or 1: contiguous rows; 32: panel lanes, see Storage) */
 } bnd_inst;
 
 /* Scheduling knobs (all optional; zero fields take the library defaults). */
@@ -102,8 +125,11 @@ typedef struct bnd_plan bnd_plan;
  * warm-up (which the check excludes).
  *
  * bnd_plan_create copies `inst` (HOST) and returns BND_EINVAL on a bad
- * descriptor (n < 1, l < 0 or > 1024, ld < n, ldr < n when k > 0, k < 0 or
- * k > 64, count < 0).  bnd_plan_workspace_bytes gives the device workspace the
+ * descriptor (n < 1, l < 0 or > 1024, cs < 0, ld < n cs, ldr < n cs when
+ * k > 0, k < 0 or k > 64, count < 0).  A batch whose column strides are not
+ * all 1 is planned as panels when every descriptor has cs = 32 and ld, ldr
+ * multiples of 32 (groups as in Storage), else as a general strided batch
+ * (direct kernels).  bnd_plan_workspace_bytes gives the device workspace the
  * plan needs; bnd_plan_bind uploads the plan's tables into that caller-owned
  * workspace on `stream` and returns once the copies are complete (it
  * synchronises `stream`; it is a set-up call, not an operator); `ws` must be
@@ -120,6 +146,9 @@ void bnd_plan_destroy(bnd_plan *plan);
 /* Number of chains (lanes of work) and warp tasks of the plan (for reporting). */
 int64_t bnd_plan_chains(const bnd_plan *plan);
 int64_t bnd_plan_tasks(const bnd_plan *plan);
+/* Arrangement the plan recognised: 0 = rows (cs = 1), 1 = panels (cs = 32
+ * groups), 2 = general strides; -1 for a NULL plan. */
+int32_t bnd_plan_layout(const bnd_plan *plan);
 /* Number of segments rerun by the verify pass of the last launch of the given
  * sweep kind (0 = Cholesky forward sweep, 1 = subset-inverse sweep,
  * 2 = subset-inverse adjoint sweep, 3 = Cholesky adjoint sweep, 4 = forward

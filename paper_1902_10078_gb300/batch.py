@@ -1,14 +1,19 @@
 """Pooled HBM layout of a batch of banded instances, and plan ownership.
 
 A batch of ``count`` instances (order n_i, bandwidth l_i, k right-hand sides)
-lives in two kinds of pools:
+lives in two kinds of pools, in one of two arrangements:
 
-* band pools: instance i occupies ``rows * ld_i`` elements starting at
-  ``band_i``; row d (a diagonal, Sec. 4.3 storage) is contiguous;
-  ``ld_i = round_up(n_i, align)`` and every offset is a multiple of ``align``
-  elements, so each diagonal starts on a 128-byte boundary.
-* RHS pools: instance i occupies ``k * ldr_i`` elements from ``rhs_i``,
+* rows (``panels=False``): instance i occupies ``rows_i * ld_i`` elements of a
+  band pool from ``band_i``; row d (a diagonal, Sec. 4.3 storage) is
+  contiguous; ``ld_i = round_up(n_i, align)`` and every offset is a multiple
+  of ``align`` elements.  RHS pools: ``k * ldr_i`` elements from ``rhs_i``,
   column r contiguous.
+* panels (``panels=True``): consecutive instances of equal bandwidth form
+  groups of up to 32; lane p of a group stores element (d, j) at
+  ``band_g + p + d * ld_g + 32 j`` (column stride 32), so column j of the
+  group's 32 instances is 32 adjacent elements.  ``ld_g = 32 * N_g`` with
+  ``N_g`` the group's largest n rounded up to 4.  Order the instances with
+  ``panel_order`` so that groups are full and their n are close.
 
 ``rows`` is ``l_i + 1 + extra_rows`` (``extra_rows`` > 0 leaves room for
 product operands with a wider band).  Host-side packing helpers move numpy
@@ -23,14 +28,21 @@ from . import binding as B
 
 TORCH_DT = {B.BND_F32: torch.float32, B.BND_F64: torch.float64}
 NP_DT = {B.BND_F32: np.float32, B.BND_F64: np.float64}
+PANEL_LANES = 32
 
 
 def _round_up(x, a):
     return (x + a - 1) // a * a
 
 
+def panel_order(ns, ls):
+    """Instance order that fills panel groups: by bandwidth, then longest first."""
+    return sorted(range(len(ns)), key=lambda i: (int(ls[i]), -int(ns[i]), i))
+
+
 class Layout:
-    def __init__(self, ns, ls, k: int, dtype: int = B.BND_F32, extra_rows: int = 0, align: int = 32):
+    def __init__(self, ns, ls, k: int, dtype: int = B.BND_F32, extra_rows: int = 0, align: int = 32,
+                 panels: bool = False):
         self.ns = [int(n) for n in ns]
         self.ls = [int(l) for l in ls]
         self.count = len(self.ns)
@@ -38,20 +50,42 @@ class Layout:
         self.dtype = dtype
         self.extra_rows = int(extra_rows)
         self.align = int(align)
-        self.ld = [_round_up(n, align) for n in self.ns]
+        self.panels = bool(panels)
         self.rows = [l + 1 + self.extra_rows for l in self.ls]
-        self.band_off = []
-        o = 0
-        for i in range(self.count):
-            self.band_off.append(o)
-            o += self.rows[i] * self.ld[i]
-        self.band_elems = max(o, 1)
-        self.rhs_off = []
-        o = 0
-        for i in range(self.count):
-            self.rhs_off.append(o)
-            o += max(self.k, 1) * self.ld[i]
-        self.rhs_elems = max(o, 1)
+        self.cs = PANEL_LANES if self.panels else 1
+        kk = max(self.k, 1)
+        self.band_off, self.rhs_off, self.ld = [], [], []
+        self.group, self.lane, self.groups = [], [], []     # panels: group id / lane of each instance
+        ob = orr = 0
+        if not self.panels:
+            for i in range(self.count):
+                ld = _round_up(self.ns[i], align)
+                self.ld.append(ld)
+                self.band_off.append(ob)
+                self.rhs_off.append(orr)
+                ob += self.rows[i] * ld
+                orr += kk * ld
+        else:
+            i = 0
+            while i < self.count:
+                j = i
+                while j < self.count and j - i < PANEL_LANES and self.ls[j] == self.ls[i]:
+                    j += 1
+                ng = _round_up(max(self.ns[i:j]), 4)
+                ld = PANEL_LANES * ng
+                g = len(self.groups)
+                self.groups.append((i, j, ob, orr, ng))
+                for q in range(i, j):
+                    self.ld.append(ld)
+                    self.band_off.append(ob + (q - i))
+                    self.rhs_off.append(orr + (q - i))
+                    self.group.append(g)
+                    self.lane.append(q - i)
+                ob = _round_up(ob + self.rows[i] * ld, align)
+                orr = _round_up(orr + kk * ld, align)
+                i = j
+        self.band_elems = max(ob, 1)
+        self.rhs_elems = max(orr, 1)
 
     @property
     def torch_dtype(self):
@@ -63,7 +97,26 @@ class Layout:
 
     def insts(self):
         return [dict(n=self.ns[i], l=self.ls[i], band=self.band_off[i], ld=self.ld[i],
-                     rhs=self.rhs_off[i], ldr=self.ld[i]) for i in range(self.count)]
+                     rhs=self.rhs_off[i], ldr=self.ld[i], cs=self.cs) for i in range(self.count)]
+
+    # --- views of one instance inside a flat pool (numpy array or tensor) ---
+    def band_view(self, pool, i):
+        """(rows_i, n_i) strided view of instance i's band region."""
+        n, rows, ld = self.ns[i], self.rows[i], self.ld[i]
+        if not self.panels:
+            o = self.band_off[i]
+            return pool[o:o + rows * ld].reshape(rows, ld)[:, :n]
+        _, _, ob, _, ng = self.groups[self.group[i]]
+        return pool[ob:ob + rows * ld].reshape(rows, ng, PANEL_LANES)[:, :n, self.lane[i]]
+
+    def rhs_view(self, pool, i):
+        """(k, n_i) strided view of instance i's RHS block."""
+        n, ld, kk = self.ns[i], self.ld[i], max(self.k, 1)
+        if not self.panels:
+            o = self.rhs_off[i]
+            return pool[o:o + kk * ld].reshape(kk, ld)[:, :n]
+        _, _, _, orr, ng = self.groups[self.group[i]]
+        return pool[orr:orr + kk * ld].reshape(kk, ng, PANEL_LANES)[:, :n, self.lane[i]]
 
     # --- pools -------------------------------------------------------------
     def band_pool(self, device="cuda", fill=0.0):
@@ -77,9 +130,7 @@ class Layout:
         pool = np.full(self.band_elems, fill, dtype=self.np_dtype)
         for i, a in enumerate(arrays):
             a = np.asarray(a)
-            r, n, ld, o = a.shape[0], self.ns[i], self.ld[i], self.band_off[i]
-            view = pool[o:o + self.rows[i] * ld].reshape(self.rows[i], ld)
-            view[:r, :n] = a
+            self.band_view(pool, i)[: a.shape[0]] = a
         return pool
 
     def unpack_band(self, pool, rows=None):
@@ -87,8 +138,7 @@ class Layout:
         out = []
         for i in range(self.count):
             r = self.ls[i] + 1 if rows is None else rows
-            ld, o = self.ld[i], self.band_off[i]
-            out.append(pool[o:o + self.rows[i] * ld].reshape(self.rows[i], ld)[:r, : self.ns[i]].astype(np.float64))
+            out.append(np.array(self.band_view(pool, i)[:r], dtype=np.float64))
         return out
 
     def pack_rhs(self, arrays, fill=0.0) -> np.ndarray:
@@ -96,18 +146,12 @@ class Layout:
         for i, a in enumerate(arrays):
             a = np.asarray(a)
             a = a[None] if a.ndim == 1 else a
-            ld, o = self.ld[i], self.rhs_off[i]
-            view = pool[o:o + self.k * ld].reshape(self.k, ld)
-            view[: a.shape[0], : self.ns[i]] = a
+            self.rhs_view(pool, i)[: a.shape[0]] = a
         return pool
 
     def unpack_rhs(self, pool):
         pool = pool.detach().cpu().numpy() if isinstance(pool, torch.Tensor) else pool
-        out = []
-        for i in range(self.count):
-            ld, o = self.ld[i], self.rhs_off[i]
-            out.append(pool[o:o + self.k * ld].reshape(self.k, ld)[:, : self.ns[i]].astype(np.float64))
-        return out
+        return [np.array(self.rhs_view(pool, i)[: self.k], dtype=np.float64) for i in range(self.count)]
 
     def to_device(self, host: np.ndarray, device="cuda"):
         return torch.from_numpy(host).to(device)

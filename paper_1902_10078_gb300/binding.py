@@ -16,12 +16,13 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_libbanded.so")
 
 BND_F32, BND_F64 = 0, 1
+LAYOUT_ROWS, LAYOUT_PANELS, LAYOUT_STRIDED = 0, 1, 2
 STATUS = {0: "BND_OK", 1: "BND_EINVAL", 2: "BND_ENOTSPD", 3: "BND_ECUDA", 4: "BND_ETIMEOUT", 5: "BND_EALIGN"}
 
 # Every symbol include/banded.h declares (checked by the ABI tests).
 EXPORTS = [
     "bnd_plan_create", "bnd_plan_workspace_bytes", "bnd_plan_bind", "bnd_plan_destroy",
-    "bnd_plan_chains", "bnd_plan_tasks", "bnd_plan_fixups",
+    "bnd_plan_chains", "bnd_plan_tasks", "bnd_plan_layout", "bnd_plan_fixups",
     "banded_cholesky", "banded_cholesky_vjp", "banded_solve", "banded_solve_vjp",
     "banded_subset_inverse", "banded_subset_inverse_vjp",
     "banded_gmm_forward", "banded_gmm_backward",
@@ -39,7 +40,7 @@ class BandedError(RuntimeError):
 
 class bnd_inst(C.Structure):
     _fields_ = [("n", C.c_int64), ("band", C.c_int64), ("ld", C.c_int64), ("rhs", C.c_int64),
-                ("ldr", C.c_int64), ("l", C.c_int32), ("reserved", C.c_int32)]
+                ("ldr", C.c_int64), ("l", C.c_int32), ("cs", C.c_int32)]
 
 
 class bnd_tuning(C.Structure):
@@ -67,6 +68,7 @@ def lib():
         "bnd_plan_destroy": (None, [_vp]),
         "bnd_plan_chains": (C.c_int64, [_vp]),
         "bnd_plan_tasks": (C.c_int64, [_vp]),
+        "bnd_plan_layout": (_i32, [_vp]),
         "bnd_plan_fixups": (_i32, [_vp, _i32, C.POINTER(C.c_int64), _vp]),
         "banded_cholesky": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
         "banded_cholesky_vjp": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
@@ -123,7 +125,7 @@ def bnd_plan_create(dtype: int, insts, k: int, tuning=None):
     arr = (bnd_inst * max(1, len(insts)))()
     for i, d in enumerate(insts):
         arr[i] = bnd_inst(int(d["n"]), int(d["band"]), int(d["ld"]), int(d.get("rhs", 0)), int(d.get("ldr", d["n"])),
-                          int(d["l"]), 0)
+                          int(d["l"]), int(d.get("cs", 1)))
     tp = None
     if tuning is not None:
         tp = C.pointer(bnd_tuning(int(tuning.get("seg_len", 0)), int(tuning.get("warmup", 0)),
@@ -152,6 +154,11 @@ def bnd_plan_chains(plan) -> int:
 
 def bnd_plan_tasks(plan) -> int:
     return int(lib().bnd_plan_tasks(plan))
+
+
+def bnd_plan_layout(plan) -> int:
+    """0: rows (cs = 1), 1: panels (cs = 32 groups), 2: general strides."""
+    return int(lib().bnd_plan_layout(plan))
 
 
 def bnd_plan_fixups(plan, kind: int, stream=None) -> int:

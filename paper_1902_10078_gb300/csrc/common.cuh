@@ -24,6 +24,7 @@ struct Chain {
 // Per-instance data uploaded to the workspace.
 struct InstDev {
     int64_t n, band, ld, rhs, ldr;
+    int64_t cs;        // column stride of the band and RHS block (1: contiguous rows)
     int32_t l;
     int32_t nseg;      // number of row segments
     int64_t seg0;      // global id of the instance's first segment (ids are consecutive)
@@ -32,10 +33,20 @@ struct InstDev {
 };
 
 // A warp task: 32 consecutive entries of the chain table (all the same l).
+// In a panel plan, chain p of a task is lane p of one instance group, all at
+// the same segment, and the task carries the group's panel geometry.
 struct Task {
     int32_t chain0;    // first chain index
     int32_t l;         // bandwidth shared by the task's chains
+    int64_t gband;     // panel plans: band offset of lane 0 of the group
+    int64_t grhs;      // panel plans: RHS offset of lane 0 of the group
+    int64_t gld, gldr; // panel plans: row strides of the group
+    int64_t gn;        // panel plans: rows present in the group (its largest n)
 };
+
+// Arrangements of a batch in its pools.
+enum : int32_t { kLayoutRows = 0, kLayoutPanels = 1, kLayoutStrided = 2 };
+constexpr int kPanelLanes = 32;    // column stride of a panel group
 
 // Sweep kinds (for state snapshots and fixup counters).
 enum SweepKind : int32_t { kSweepChol = 0, kSweepTaka = 1, kSweepTakaBar = 2, kSweepCholBar = 3,
@@ -104,6 +115,7 @@ struct bnd_plan {
     // tasks are grouped by bandwidth class: class 0 = generic (l = 0 or l > kRegMaxL),
     // class c = bandwidth c; class c owns tasks [class_task0[c], class_task0[c+1])
     int32_t class_task0[bnd::kRegMaxL + 2];
+    int32_t layout;            // kLayoutRows, kLayoutPanels or kLayoutStrided
     int32_t staged_ok;         // every offset / stride allows 16-byte tiles
     int32_t force_direct;      // tuning: never use the staged kernels
     cudaStream_t side[bnd::kRegMaxL + 1];

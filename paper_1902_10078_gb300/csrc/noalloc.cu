@@ -57,7 +57,7 @@ __global__ void noalloc_solve_kernel(int64_t n, int32_t l, const T *Lm, int64_t 
     A.rhs0 = 0;
     A.kk = 1;
     ChainCtx c{};
-    c.n = n; c.band = 0; c.ld = ld; c.rhs = 0; c.ldr = n; c.l = l;
+    c.n = n; c.band = 0; c.ld = ld; c.rhs = 0; c.ldr = n; c.cs = 1; c.l = l;
     c.a = 0; c.b = n; c.gseg = 0; c.warm = 0; c.inst = 0;
     c.first = true; c.last = true;
     if constexpr (L >= 1) {

@@ -2,6 +2,7 @@
 // grouping of equal-bandwidth chains into warp tasks, longest-first task
 // order, and the device workspace layout.
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -31,6 +32,56 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+namespace {
+
+int64_t col_stride(const bnd_inst &I) { return I.cs <= 1 ? 1 : (int64_t)I.cs; }
+
+// Panel groups: a group is a run of at most 32 consecutive descriptors with
+// column stride 32 whose band (and RHS) offsets increase by one and which
+// share l, ld and ldr; lane p is the p-th descriptor of the run.  Fills
+// `groups` with the first descriptor of every group (plus `count` at the
+// end) and returns false if some descriptor cannot belong to a panel.
+// *aligned tells whether every group base allows 16-byte copies.
+bool detect_panels(int32_t count, const bnd_inst *inst, int32_t k, int64_t tw, std::vector<int32_t> &groups,
+                   bool *aligned) {
+    *aligned = true;
+    groups.clear();
+    for (int32_t i = 0; i < count; ++i) {
+        const bnd_inst &I = inst[i];
+        if (I.cs != kPanelLanes || I.ld % kPanelLanes || (k > 0 && I.ldr % kPanelLanes)) return false;
+        bool cont = false;
+        if (!groups.empty()) {
+            const int32_t g0 = groups.back();
+            const bnd_inst &H = inst[g0];
+            const int64_t p = i - g0;
+            cont = p < kPanelLanes && I.l == H.l && I.ld == H.ld && I.band == H.band + p &&
+                   (k == 0 || (I.ldr == H.ldr && I.rhs == H.rhs + p));
+        }
+        if (!cont) {
+            groups.push_back(i);
+            if (I.band % tw || (k > 0 && I.rhs % tw)) *aligned = false;
+        }
+    }
+    groups.push_back(count);
+    return true;
+}
+
+// Segment count and length for `n` rows (nearest count of seg_len-row
+// segments, length a multiple of 4 rows); one segment when not split.
+void segmentation(int64_t n, int64_t seg_len, int64_t warm, bool reg, int64_t *nseg_out, int64_t *len_out) {
+    int64_t nseg = 1;
+    if (reg && seg_len > 0 && n > seg_len + warm) {
+        nseg = (n + seg_len / 2) / seg_len;
+        if (nseg < 1) nseg = 1;
+    }
+    int64_t len = (n + nseg - 1) / nseg;
+    len = (len + 3) / 4 * 4;
+    *nseg_out = (n + len - 1) / len;
+    *len_out = len;
+}
+
+}  // namespace
+
 extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t count, const bnd_inst *inst,
                                       int32_t k, const bnd_tuning *tuning) {
     if (!out) return BND_EINVAL;
@@ -38,10 +89,15 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     if (dtype != BND_F32 && dtype != BND_F64) return BND_EINVAL;
     if (count < 0 || (count > 0 && !inst)) return BND_EINVAL;
     if (k < 0 || k > kMaxRhs) return BND_EINVAL;
+    bool all_rows = true;
     for (int32_t i = 0; i < count; ++i) {
         const bnd_inst &I = inst[i];
-        if (I.n < 1 || I.l < 0 || I.l > kMaxBand || I.ld < I.n || I.band < 0) return BND_EINVAL;
-        if (k > 0 && (I.ldr < I.n || I.rhs < 0)) return BND_EINVAL;
+        if (I.cs < 0) return BND_EINVAL;
+        const int64_t cs = col_stride(I);
+        if (I.n < 1 || I.l < 0 || I.l > kMaxBand || I.band < 0) return BND_EINVAL;
+        if (I.n > INT64_MAX / cs || I.ld < I.n * cs) return BND_EINVAL;
+        if (k > 0 && (I.ldr < I.n * cs || I.rhs < 0)) return BND_EINVAL;
+        if (cs != 1) all_rows = false;
     }
     bnd_plan *p = new (std::nothrow) bnd_plan();
     if (!p) return BND_EINVAL;
@@ -60,6 +116,19 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     }
     const int64_t tw = 16 / (int64_t)esz;                 // elements per 16-byte tile
     p->staged_ok = 1;
+    std::vector<int32_t> groups;          // panel plans: first descriptor of each group, then count
+    std::vector<int32_t> group_of((size_t)count, 0);
+    if (all_rows) {
+        p->layout = kLayoutRows;
+    } else {
+        bool aligned = true;
+        p->layout = detect_panels(count, inst, k, tw, groups, &aligned) ? kLayoutPanels : kLayoutStrided;
+        if (p->layout == kLayoutStrided || !aligned) p->staged_ok = 0;
+        if (p->layout == kLayoutPanels)
+            for (size_t g = 0; g + 1 < groups.size(); ++g)
+                for (int32_t i = groups[g]; i < groups[g + 1]; ++i) group_of[(size_t)i] = (int32_t)g;
+    }
+    const bool panels = p->layout == kLayoutPanels;
 
     std::vector<InstDev> idev((size_t)count);
     int64_t nsegs = 0;
@@ -70,23 +139,28 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         const bnd_inst &I = inst[i];
         InstDev &D = idev[(size_t)i];
         D.n = I.n; D.band = I.band; D.ld = I.ld; D.rhs = I.rhs; D.ldr = I.ldr; D.l = I.l;
+        D.cs = col_stride(I);
         const bool reg = I.l >= 1 && I.l <= kRegMaxL;
         if (!reg) has_generic = true;
         D.warm = p->warm > 0 ? ((int64_t)p->warm + 3) / 4 * 4 : default_warm(dtype, I.l);
-        int64_t nseg = 1;
-        if (reg && p->seg_len > 0 && I.n > p->seg_len + D.warm) {
-            nseg = (I.n + p->seg_len / 2) / p->seg_len;     // nearest segment count
-            if (nseg < 1) nseg = 1;
+        int64_t nseg = 1, len = I.n;
+        if (panels) {
+            // one segment length for the whole group, set by its longest member
+            const int32_t g = group_of[(size_t)i], g0 = groups[(size_t)g], g1 = groups[(size_t)g + 1];
+            int64_t gn = 0;
+            for (int32_t q = g0; q < g1; ++q) gn = std::max(gn, inst[q].n);
+            int64_t gseg = 1;
+            segmentation(gn, p->seg_len, D.warm, reg, &gseg, &len);
+            nseg = (I.n + len - 1) / len;
+        } else {
+            segmentation(I.n, p->seg_len, D.warm, reg, &nseg, &len);
+            if (I.band % tw || I.ld % tw || (k > 0 && (I.rhs % tw || I.ldr % tw))) p->staged_ok = 0;
         }
-        int64_t len = (I.n + nseg - 1) / nseg;
-        len = (len + 3) / 4 * 4;                              // multiple of 4 rows
-        nseg = (I.n + len - 1) / len;
         D.nseg = (int32_t)nseg;
         D.seg_len = len;
         D.seg0 = nsegs;
         nsegs += nseg;
         max_l = std::max(max_l, I.l);
-        if (I.band % tw || I.ld % tw || (k > 0 && (I.rhs % tw || I.ldr % tw))) p->staged_ok = 0;
         band_extent = std::max(band_extent, I.band + (int64_t)(I.l + 1) * I.ld);
         if (k > 0) rhs_extent = std::max(rhs_extent, I.rhs + (int64_t)k * I.ldr);
     }
@@ -96,43 +170,85 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->rhs_pool_elems = rhs_extent;
     p->snap_words = snap_words_for(std::min(max_l, kRegMaxL), std::max(k, kMaxK));
 
-    // chains: one per segment, grouped by l, longest first inside a group
-    std::vector<Chain> ch;
-    ch.reserve((size_t)nsegs);
+    struct TaskTmp { std::vector<Chain> c; int32_t l; int32_t cls; double cost; Task geo; };
+    auto class_of = [](int l) { return (l >= 1 && l <= kRegMaxL) ? l : 0; };
+    auto chain_rows = [&](const Chain &c) {
+        return c.b - c.a + (c.seg > 0 ? idev[(size_t)c.inst].warm : 0);
+    };
+    auto pad_chain = []() { Chain pad; pad.inst = -1; pad.seg = 0; pad.a = pad.b = 0; return pad; };
+    std::vector<TaskTmp> tt;
+    auto group_tasks_by_l = [&](std::vector<Chain> &ch) {
+        // chains of equal l, longest first, 32 to a task
+        std::stable_sort(ch.begin(), ch.end(), [&](const Chain &x, const Chain &y) {
+            const int lx = idev[(size_t)x.inst].l, ly = idev[(size_t)y.inst].l;
+            if (lx != ly) return lx < ly;
+            return (x.b - x.a) > (y.b - y.a);
+        });
+        for (size_t s = 0; s < ch.size();) {
+            const int32_t l = idev[(size_t)ch[s].inst].l;
+            TaskTmp t;
+            t.l = l;
+            t.cls = class_of(l);
+            t.cost = 0;
+            std::memset(&t.geo, 0, sizeof(t.geo));
+            while (s < ch.size() && (int)t.c.size() < kWarp && idev[(size_t)ch[s].inst].l == l) {
+                t.cost = std::max(t.cost, (double)chain_rows(ch[s]) * (double)(l + 2) * (double)(l + 2));
+                t.c.push_back(ch[s]);
+                ++s;
+            }
+            while ((int)t.c.size() < kWarp) t.c.push_back(pad_chain());
+            tt.push_back(std::move(t));
+        }
+    };
+    std::vector<Chain> loose;      // chains not bound to a panel lane
     for (int32_t i = 0; i < count; ++i) {
         const InstDev &D = idev[(size_t)i];
+        if (panels && class_of(D.l) != 0) continue;
         for (int32_t s = 0; s < D.nseg; ++s) {
             Chain c;
             c.inst = i; c.seg = s;
             c.a = (int64_t)s * D.seg_len;
             c.b = std::min(c.a + D.seg_len, D.n);
-            ch.push_back(c);
+            loose.push_back(c);
         }
     }
-    std::stable_sort(ch.begin(), ch.end(), [&](const Chain &x, const Chain &y) {
-        const int lx = idev[(size_t)x.inst].l, ly = idev[(size_t)y.inst].l;
-        if (lx != ly) return lx < ly;
-        return (x.b - x.a) > (y.b - y.a);
-    });
-    // tasks of 32 chains with equal l
-    struct TaskTmp { std::vector<Chain> c; int32_t l; int32_t cls; double cost; };
-    auto class_of = [](int l) { return (l >= 1 && l <= kRegMaxL) ? l : 0; };
-    std::vector<TaskTmp> tt;
-    for (size_t s = 0; s < ch.size();) {
-        const int32_t l = idev[(size_t)ch[s].inst].l;
-        TaskTmp t;
-        t.l = l;
-        t.cls = class_of(l);
-        t.cost = 0;
-        while (s < ch.size() && (int)t.c.size() < kWarp && idev[(size_t)ch[s].inst].l == l) {
-            const Chain &c = ch[s];
-            int64_t rows = c.b - c.a + (c.seg > 0 ? idev[(size_t)c.inst].warm : 0);
-            t.cost = std::max(t.cost, (double)rows * (double)(l + 2) * (double)(l + 2));
-            t.c.push_back(c);
-            ++s;
+    group_tasks_by_l(loose);
+    if (panels) {
+        // one task per (group, segment): chain p is lane p of the group at that segment
+        for (size_t g = 0; g + 1 < groups.size(); ++g) {
+            const int32_t g0 = groups[g], g1 = groups[g + 1];
+            const InstDev &H = idev[(size_t)g0];
+            if (class_of(H.l) == 0) continue;
+            int32_t gseg = 0;
+            int64_t gn = 0;
+            for (int32_t q = g0; q < g1; ++q) {
+                gseg = std::max(gseg, idev[(size_t)q].nseg);
+                gn = std::max(gn, idev[(size_t)q].n);
+            }
+            for (int32_t s = 0; s < gseg; ++s) {
+                TaskTmp t;
+                t.l = H.l;
+                t.cls = class_of(H.l);
+                t.cost = 0;
+                t.geo.chain0 = 0; t.geo.l = H.l;
+                t.geo.gband = H.band; t.geo.grhs = H.rhs; t.geo.gld = H.ld; t.geo.gldr = H.ldr; t.geo.gn = gn;
+                for (int32_t p2 = 0; p2 < kWarp; ++p2) {
+                    const int32_t q = g0 + p2;
+                    if (q < g1 && s < idev[(size_t)q].nseg) {
+                        const InstDev &D = idev[(size_t)q];
+                        Chain c;
+                        c.inst = q; c.seg = s;
+                        c.a = (int64_t)s * D.seg_len;
+                        c.b = std::min(c.a + D.seg_len, D.n);
+                        t.cost = std::max(t.cost, (double)chain_rows(c) * (double)(H.l + 2) * (double)(H.l + 2));
+                        t.c.push_back(c);
+                    } else {
+                        t.c.push_back(pad_chain());
+                    }
+                }
+                tt.push_back(std::move(t));
+            }
         }
-        while ((int)t.c.size() < kWarp) { Chain pad; pad.inst = -1; pad.seg = 0; pad.a = pad.b = 0; t.c.push_back(pad); }
-        tt.push_back(std::move(t));
     }
     std::stable_sort(tt.begin(), tt.end(), [](const TaskTmp &x, const TaskTmp &y) {
         if (x.cls != y.cls) return x.cls < y.cls;
@@ -155,6 +271,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     if (!p->inst || !p->chains || !p->tasks) { bnd_plan_destroy(p); return BND_EINVAL; }
     if (count) std::memcpy(p->inst, idev.data(), sizeof(InstDev) * (size_t)count);
     for (size_t t = 0; t < tt.size(); ++t) {
+        p->tasks[t] = tt[t].geo;
         p->tasks[t].chain0 = (int32_t)(t * kWarp);
         p->tasks[t].l = tt[t].l;
         for (int c = 0; c < kWarp; ++c) p->chains[t * kWarp + c] = tt[t].c[(size_t)c];
@@ -193,6 +310,8 @@ extern "C" size_t bnd_plan_workspace_bytes(const bnd_plan *p) { return p ? p->ws
 extern "C" int64_t bnd_plan_chains(const bnd_plan *p) { return p ? p->nsegs : 0; }
 
 extern "C" int64_t bnd_plan_tasks(const bnd_plan *p) { return p ? p->ntasks : 0; }
+
+extern "C" int32_t bnd_plan_layout(const bnd_plan *p) { return p ? p->layout : -1; }
 
 extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void *stream) {
     if (!p || (!ws && p->ws_bytes) || ws_bytes < p->ws_bytes) return BND_EINVAL;

@@ -10,13 +10,13 @@ namespace bnd {
 // Element (i, j) of op(M) for a general band (lo, up) stored with
 // M[i, j] = M'[up + i - j][j]; zero outside the band or the matrix.
 template <typename T>
-__device__ __forceinline__ T band_get(const T *M, int64_t ld, int lo, int up, bool trans, int64_t n,
+__device__ __forceinline__ T band_get(const T *M, int64_t ld, int64_t cs, int lo, int up, bool trans, int64_t n,
                                       int64_t i, int64_t j) {
     if (trans) { int64_t t = i; i = j; j = t; }
     if (i < 0 || j < 0 || i >= n || j >= n) return T(0);
     const int64_t dd = i - j;
     if (dd > lo || -dd > up) return T(0);
-    return M[(int64_t)(up + dd) * ld + j];
+    return M[(int64_t)(up + dd) * ld + j * cs];
 }
 
 __device__ __forceinline__ int find_instance(const int64_t *prefix, int count, int64_t tile) {
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) product_kernel(PlanDev P, ProdArgs<T> A) 
     const InstDev I = P.inst[inst];
     const int64_t j = (tile - P.tile_prefix[inst]) * 256 + threadIdx.x;
     if (j >= I.n) return;
-    const int64_t n = I.n, ld = I.ld;
+    const int64_t n = I.n, ld = I.ld, cs = I.cs;
     const T *Am = A.A + I.band;
     const T *Bm = A.B + I.band;
     T *Cm = A.C + I.band;
@@ -50,11 +50,11 @@ __global__ void __launch_bounds__(256) product_kernel(PlanDev P, ProdArgs<T> A) 
             const int64_t t0 = imax64(imax64(i - alo_op, j - bup_op), 0);
             const int64_t t1 = imin64(imin64(i + aup_op, j + blo_op), n - 1);
             for (int64_t t = t0; t <= t1; ++t)
-                s = fma(band_get(Am, ld, alo, A.aup, A.transA != 0, n, i, t),
-                        band_get(Bm, ld, blo, A.bup, A.transB != 0, n, t, j), s);
+                s = fma(band_get(Am, ld, cs, alo, A.aup, A.transA != 0, n, i, t),
+                        band_get(Bm, ld, cs, blo, A.bup, A.transB != 0, n, t, j), s);
             s *= A.alpha;
         }
-        T *p = &Cm[(int64_t)r * ld + j];
+        T *p = &Cm[(int64_t)r * ld + j * cs];
         *p = (A.acc && i >= 0 && i < n) ? (*p + s) : s;
     }
 }
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) outer_kernel(PlanDev P, OuterArgs<T> A) {
     const InstDev I = P.inst[inst];
     const int64_t j = (tile - P.tile_prefix[inst]) * 256 + threadIdx.x;
     if (j >= I.n) return;
-    const int64_t n = I.n, ld = I.ld;
+    const int64_t n = I.n, ld = I.ld, cs = I.cs;
     const T *M = A.M + I.rhs;
     const T *V = A.V + I.rhs;
     T *Cm = A.C + I.band;
@@ -76,10 +76,10 @@ __global__ void __launch_bounds__(256) outer_kernel(PlanDev P, OuterArgs<T> A) {
         const int64_t i = j + (r - A.cup);
         T s = T(0);
         if (i >= 0 && i < n) {
-            for (int c = 0; c < A.k; ++c) s = fma(M[(int64_t)c * I.ldr + i], V[(int64_t)c * I.ldr + j], s);
+            for (int c = 0; c < A.k; ++c) s = fma(M[(int64_t)c * I.ldr + i * cs], V[(int64_t)c * I.ldr + j * cs], s);
             s *= A.alpha;
         }
-        T *p = &Cm[(int64_t)r * ld + j];
+        T *p = &Cm[(int64_t)r * ld + j * cs];
         *p = (A.acc && i >= 0 && i < n) ? (*p + s) : s;
     }
 }
@@ -102,9 +102,9 @@ __global__ void __launch_bounds__(256) matvec_kernel(PlanDev P, MatvecArgs<T> A)
     for (int c = 0; c < A.k; ++c) {
         T s = T(0);
         for (int64_t t = t0; t <= t1; ++t)
-            s = fma(band_get(Am, I.ld, alo, A.aup, A.transA != 0, n, i, t), V[(int64_t)c * I.ldr + t], s);
+            s = fma(band_get(Am, I.ld, I.cs, alo, A.aup, A.transA != 0, n, i, t), V[(int64_t)c * I.ldr + t * I.cs], s);
         s *= A.alpha;
-        T *p = &Po[(int64_t)c * I.ldr + i];
+        T *p = &Po[(int64_t)c * I.ldr + i * I.cs];
         *p = A.acc ? (*p + s) : s;
     }
 }
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) band_add_kernel(PlanDev P, const T *src, 
     const int64_t j = (tile - P.tile_prefix[inst]) * 256 + threadIdx.x;
     if (j >= I.n) return;
     for (int d = 0; d <= I.l; ++d) {
-        const int64_t o = I.band + (int64_t)d * I.ld + j;
+        const int64_t o = I.band + (int64_t)d * I.ld + j * I.cs;
         dst[o] = (j + d < I.n) ? dst[o] + src[o] : T(0);
     }
 }

@@ -32,6 +32,7 @@
 // segments from the exact end snapshot of their predecessor.
 #pragma once
 
+#include <climits>
 #include <utility>
 
 #include "common.cuh"
@@ -92,6 +93,7 @@ template <int L> struct Tri { static constexpr int N = L * (L + 1) / 2; };
 // Per-chain context: instance view plus the segment's rows.
 struct ChainCtx {
     int64_t n, band, ld, rhs, ldr;
+    int64_t cs;          // column stride
     int64_t a, b;        // output rows [a, b)
     int64_t gseg;        // global segment id
     int64_t warm;        // warm-up rows of a speculative start
@@ -114,6 +116,24 @@ __device__ inline bool snap_equal(const T *x, const T *y, int64_t words) {
         else eq &= (__double_as_longlong((double)x[w]) == __double_as_longlong((double)y[w]));
     }
     return eq;
+}
+
+// Warp-wide minimum / maximum (every lane of the warp must call).
+__device__ __forceinline__ int64_t warp_min64(int64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ int64_t warp_max64(int64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
 }
 
 // Bounds guard of a step: boundary tiles check, interior tiles compile the check away.
@@ -215,9 +235,9 @@ struct FwdReg {
         _Pragma("unroll") for (int t = 1; t <= L; ++t)
             _Pragma("unroll") for (int q = t; q <= L; ++q) {
                 int64_t col = i0 + t, row = i0 + q;
-                sblk[tri(t - 1, q - 1, L)] = (row < c.n) ? S[(int64_t)(q - t) * c.ld + col] : T(0);
+                sblk[tri(t - 1, q - 1, L)] = (row < c.n) ? S[(int64_t)(q - t) * c.ld + col * c.cs] : T(0);
             }
-        _Pragma("unroll") for (int d = 0; d < L; ++d) srow[d] = (i0 + d < c.n) ? S[(int64_t)d * c.ld + i0] : T(0);
+        _Pragma("unroll") for (int d = 0; d < L; ++d) srow[d] = (i0 + d < c.n) ? S[(int64_t)d * c.ld + i0 * c.cs] : T(0);
     }
 
     // One column / row step.  `out` selects whether outputs are written.
@@ -389,16 +409,16 @@ struct BwdReg {
             _Pragma("unroll") for (int e = 1; e <= L; ++e)
                 _Pragma("unroll") for (int f = 0; f <= L - e; ++f) {
                     int64_t col = j0 - e, row = j0 + f;
-                    lwin[tri(e - 1, e - 1 + f, L)] = (col >= 0 && row < c.n) ? Li[(int64_t)(e + f) * c.ld + col] : T(0);
+                    lwin[tri(e - 1, e - 1 + f, L)] = (col >= 0 && row < c.n) ? Li[(int64_t)(e + f) * c.ld + col * c.cs] : T(0);
                 }
-            _Pragma("unroll") for (int d = 1; d <= L; ++d) lcol[d] = (j0 + d < c.n) ? Li[(int64_t)d * c.ld + j0] : T(0);
+            _Pragma("unroll") for (int d = 1; d <= L; ++d) lcol[d] = (j0 + d < c.n) ? Li[(int64_t)d * c.ld + j0 * c.cs] : T(0);
         }
         if (OUTER) {
             const T *Xi = A.Xin + c.rhs;
             _Pragma("unroll") for (int r = 0; r < KK; ++r) {
                 const bool on = r < A.kk;
                 int64_t co = (int64_t)(A.rhs0 + (on ? r : 0)) * c.ldr;
-                _Pragma("unroll") for (int d = 0; d < L; ++d) xin[r][d] = (on && j0 + 1 + d < c.n) ? Xi[co + j0 + 1 + d] : T(0);
+                _Pragma("unroll") for (int d = 0; d < L; ++d) xin[r][d] = (on && j0 + 1 + d < c.n) ? Xi[co + (j0 + 1 + d) * c.cs] : T(0);
             }
         }
     }
@@ -541,7 +561,7 @@ __device__ __forceinline__ ChainPtrs<T> chain_ptrs(const SweepArgs<T> &A, const 
     P.out[POOL_SOUT - POOL_LOUT] = A.Sout ? A.Sout + c.band : nullptr;
     P.out[POOL_QBAR - POOL_LOUT] = A.Qbar ? A.Qbar + c.band : nullptr;
     P.out[POOL_XOUT - POOL_LOUT] = A.Xout ? A.Xout + c.rhs : nullptr;
-    P.ld = c.ld; P.ldr = c.ldr; P.n = c.n; P.rhs0 = A.rhs0; P.acc = A.acc; P.kk = A.kk;
+    P.ld = c.ld; P.ldr = c.ldr; P.cs = c.cs; P.n = c.n; P.rhs0 = A.rhs0; P.acc = A.acc; P.kk = A.kk;
     return P;
 }
 
@@ -555,13 +575,19 @@ __device__ void run_fwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
     int64_t j0 = c.a;
     if (mode == RUN_COLD && !c.first) j0 = imax64(c.a - c.warm, 0);
     if (mode == RUN_EXACT && exact_state) s.load_state(exact_state);
-    s.preload(A, c, j0);
+    if (c.inst >= 0) s.preload(A, c, j0);
     const int64_t jend = c.b - 1;
     const int64_t m0 = floordiv(j0, TW), m1 = floordiv(jend, TW);
-    io.begin_tiles(m0, c.a, c.b);
+    int64_t w0 = m0, w1 = m1;
+    if constexpr (IO::kWarpUniform) {
+        // cooperative copies: the warp walks the union of its lanes' tiles
+        w0 = warp_min64(c.inst >= 0 ? m0 : INT64_MAX);
+        w1 = warp_max64(c.inst >= 0 ? m1 : INT64_MIN);
+    }
+    io.begin_tiles(w0, c.a, c.b);
     LogSum<T> ld;
     int32_t info = 0;
-    for (int64_t m = m0; m <= m1; ++m) {
+    for (int64_t m = w0; m <= w1; ++m) {
         io.tile_begin(m);
         const int64_t jt = m * TW;
         if (jt == c.a && !c.first) s.save(snap_ptr<T>(P, c.gseg, 0));
@@ -581,6 +607,7 @@ __device__ void run_fwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
         io.tile_end(m, has_out);
     }
     io.finish();
+    if (c.inst < 0) return;
     if (!c.last) s.save(snap_ptr<T>(P, c.gseg, 1));
     const double ldacc = ld.value();
     if (FL & F_CHOL) {
@@ -604,10 +631,15 @@ __device__ void run_bwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
     int64_t j0 = c.b - 1;
     if (mode == RUN_COLD && !c.last) j0 = imin64(c.b - 1 + c.warm, c.n - 1);
     if (mode == RUN_EXACT && exact_state) s.load_state(exact_state);
-    s.preload(A, c, j0);
+    if (c.inst >= 0) s.preload(A, c, j0);
     const int64_t m0 = floordiv(j0, TW), m1 = floordiv(c.a, TW);
-    io.begin_tiles(m0, c.a, c.b);
-    for (int64_t m = m0; m >= m1; --m) {
+    int64_t w0 = m0, w1 = m1;
+    if constexpr (IO::kWarpUniform) {
+        w0 = warp_max64(c.inst >= 0 ? m0 : INT64_MIN);
+        w1 = warp_min64(c.inst >= 0 ? m1 : INT64_MAX);
+    }
+    io.begin_tiles(w0, c.a, c.b);
+    for (int64_t m = w0; m >= w1; --m) {
         io.tile_begin(m);
         const int64_t jt = m * TW;
         if (jt + TW - 1 == c.b - 1 && !c.last) s.save(snap_ptr<T>(P, c.gseg, 0));
@@ -627,7 +659,7 @@ __device__ void run_bwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
         io.tile_end(m, has_out);
     }
     io.finish();
-    if (!c.first) s.save(snap_ptr<T>(P, c.gseg, 1));
+    if (c.inst >= 0 && !c.first) s.save(snap_ptr<T>(P, c.gseg, 1));
 }
 
 // ===========================================================================
@@ -637,7 +669,7 @@ __device__ void run_bwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
 // ===========================================================================
 template <typename T, int FL>
 __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c) {
-    const int64_t n = c.n, ld = c.ld;
+    const int64_t n = c.n, ld = c.ld, cs = c.cs;
     const int l = c.l;
     constexpr bool CHOL = (FL & F_CHOL) != 0, ALG4 = (FL & F_ALG4) != 0;
     const bool SOLVE = (FL & F_SOLVE) != 0 && P.k > 0;
@@ -646,7 +678,7 @@ __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
     int32_t info = 0;
     T *Lw = CHOL ? A.L + c.band : nullptr;
     const T *Lr = CHOL ? (const T *)(A.L + c.band) : A.Lin + c.band;
-#define LL(i_, j_) Lr[(int64_t)((i_) - (j_)) * ld + (j_)]
+#define LL(i_, j_) Lr[(int64_t)((i_) - (j_)) * ld + (j_) * cs]
     for (int64_t j = 0; j < n; ++j) {
         const int dmax = (int)imin64(l, n - 1 - j);
         T rinv;
@@ -654,7 +686,7 @@ __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
             const T *Q = A.Q + c.band;
             T s = T(0);
             for (int64_t m = imax64(j - l, 0); m < j; ++m) s = fma(LL(j, m), LL(j, m), s);
-            T piv = Q[j] - s;
+            T piv = Q[j * cs] - s;
             if (!(piv > T(0)) && info == 0) info = (int32_t)(j + 1);
             T ljj = Num<T>::sqrt_(piv);
             rinv = T(1) / ljj;
@@ -662,21 +694,21 @@ __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
             for (int d = 1; d <= dmax; ++d) {
                 T t = T(0);
                 for (int64_t m = imax64(j + d - l, 0); m < j; ++m) t = fma(LL(j + d, m), LL(j, m), t);
-                Lw[(int64_t)d * ld + j] = (Q[(int64_t)d * ld + j] - t) * rinv;
+                Lw[(int64_t)d * ld + (j) * cs] = (Q[(int64_t)d * ld + (j) * cs] - t) * rinv;
             }
-            Lw[j] = ljj;
-            for (int d = dmax + 1; d <= l; ++d) Lw[(int64_t)d * ld + j] = T(0);
+            Lw[j * cs] = ljj;
+            for (int d = dmax + 1; d <= l; ++d) Lw[(int64_t)d * ld + (j) * cs] = T(0);
         } else {
-            rinv = T(1) / Lr[j];
+            rinv = T(1) / Lr[j * cs];
         }
         if (SOLVE) {
             const T *Bi = A.Bin + c.rhs;
             T *Xo = A.Xout + c.rhs;
             for (int r = 0; r < K; ++r) {
                 int64_t co = (int64_t)(A.rhs0 + r) * c.ldr;
-                T s = Bi[co + j];
-                for (int64_t m = imax64(j - l, 0); m < j; ++m) s = fma(-LL(j, m), Xo[co + m], s);
-                Xo[co + j] = s * rinv;
+                T s = Bi[co + (j) * cs];
+                for (int64_t m = imax64(j - l, 0); m < j; ++m) s = fma(-LL(j, m), Xo[co + (m) * cs], s);
+                Xo[co + (j) * cs] = s * rinv;
             }
         }
         if (ALG4) {
@@ -688,31 +720,31 @@ __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
             T *bU = A.scratch2 + c.band;
             T *Lb = A.Lbar + c.band;
             const int64_t i = j;
-#define SYM(a_, b_) (((a_) >= (b_)) ? S[(int64_t)((a_) - (b_)) * ld + (b_)] : S[(int64_t)((b_) - (a_)) * ld + (a_)])
-#define PAIR(a_, b_) (((a_) >= (b_)) ? Pp[(int64_t)((a_) - (b_)) * ld + (b_)] : Pp[(int64_t)((b_) - (a_)) * ld + (a_)])
-            for (int q = 0; q <= dmax; ++q) Pp[(int64_t)q * ld + i] += Sb[(int64_t)q * ld + i];
-            const T b0 = Pp[i];
+#define SYM(a_, b_) (((a_) >= (b_)) ? S[(int64_t)((a_) - (b_)) * ld + (b_) * cs] : S[(int64_t)((b_) - (a_)) * ld + (a_) * cs])
+#define PAIR(a_, b_) (((a_) >= (b_)) ? Pp[(int64_t)((a_) - (b_)) * ld + (b_) * cs] : Pp[(int64_t)((b_) - (a_)) * ld + (a_) * cs])
+            for (int q = 0; q <= dmax; ++q) Pp[(int64_t)q * ld + (i) * cs] += Sb[(int64_t)q * ld + (i) * cs];
+            const T b0 = Pp[i * cs];
             for (int t = 1; t <= dmax; ++t) {
                 T Ut = LL(i + t, i) * rinv;
-                bU[(int64_t)t * ld + i] = -b0 * SYM(i, i + t);
-                Pp[(int64_t)t * ld + i] = fma(-b0, Ut, Pp[(int64_t)t * ld + i]);
+                bU[(int64_t)t * ld + (i) * cs] = -b0 * SYM(i, i + t);
+                Pp[(int64_t)t * ld + (i) * cs] = fma(-b0, Ut, Pp[(int64_t)t * ld + (i) * cs]);
             }
             for (int q = 1; q <= dmax; ++q) {
-                const T bq = Pp[(int64_t)q * ld + i];
+                const T bq = Pp[(int64_t)q * ld + (i) * cs];
                 for (int t = 1; t <= dmax; ++t) {
                     T Ut = LL(i + t, i) * rinv;
-                    bU[(int64_t)t * ld + i] = fma(-bq, SYM(i + t, i + q), bU[(int64_t)t * ld + i]);
+                    bU[(int64_t)t * ld + (i) * cs] = fma(-bq, SYM(i + t, i + q), bU[(int64_t)t * ld + (i) * cs]);
                     T &pr = PAIR(i + t, i + q);
                     pr = fma(-bq, Ut, pr);
                 }
             }
             T s = T(0);
-            for (int t = 1; t <= dmax; ++t) s = fma(bU[(int64_t)t * ld + i], LL(i + t, i), s);
+            for (int t = 1; t <= dmax; ++t) s = fma(bU[(int64_t)t * ld + (i) * cs], LL(i + t, i), s);
             const T r2 = rinv * rinv;
             const T bvec = T(-2) * b0 * r2 * rinv - s * r2;
             for (int t = 0; t <= l; ++t) {
-                T v = (t == 0) ? bvec : (t <= dmax ? bU[(int64_t)t * ld + i] * rinv : T(0));
-                T *p = &Lb[(int64_t)t * ld + i];
+                T v = (t == 0) ? bvec : (t <= dmax ? bU[(int64_t)t * ld + (i) * cs] * rinv : T(0));
+                T *p = &Lb[(int64_t)t * ld + (i) * cs];
                 *p = (t <= dmax) ? (A.acc ? (*p + v) : v) : T(0);                  // corners: 0
             }
 #undef SYM
@@ -728,40 +760,40 @@ __device__ void run_fwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
 
 template <typename T, int FL>
 __device__ void run_bwd_generic(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c) {
-    const int64_t n = c.n, ld = c.ld;
+    const int64_t n = c.n, ld = c.ld, cs = c.cs;
     const int l = c.l;
     constexpr bool TAKA = (FL & B_TAKA) != 0, ALG2 = (FL & B_ALG2) != 0;
     const bool SOLVE = (FL & B_SOLVE) != 0 && P.k > 0;
     const bool OUTER = (FL & B_OUTER) != 0 && SOLVE && ALG2;
     const int K = SOLVE ? A.kk : 0;
     const T *Lr = A.Lin + c.band;
-#define LL(i_, j_) Lr[(int64_t)((i_) - (j_)) * ld + (j_)]
+#define LL(i_, j_) Lr[(int64_t)((i_) - (j_)) * ld + (j_) * cs]
     for (int64_t j = n - 1; j >= 0; --j) {
         const int dmax = (int)imin64(l, n - 1 - j);
-        const T rinv = T(1) / Lr[j];
+        const T rinv = T(1) / Lr[j * cs];
         if (SOLVE) {
             const T *Bi = A.Bin + c.rhs;
             T *Xo = A.Xout + c.rhs;
             for (int r = 0; r < K; ++r) {
                 int64_t co = (int64_t)(A.rhs0 + r) * c.ldr;
-                T s = Bi[co + j];
-                for (int d = dmax; d >= 1; --d) s = fma(-LL(j + d, j), Xo[co + j + d], s);
-                Xo[co + j] = s * rinv;
+                T s = Bi[co + (j) * cs];
+                for (int d = dmax; d >= 1; --d) s = fma(-LL(j + d, j), Xo[co + (j + d) * cs], s);
+                Xo[co + (j) * cs] = s * rinv;
             }
         }
         if (TAKA) {
             T *So = A.Sout + c.band;
             const int64_t i = j;
-#define SIG(a_, b_) (((a_) >= (b_)) ? So[(int64_t)((a_) - (b_)) * ld + (b_)] : So[(int64_t)((b_) - (a_)) * ld + (a_)])
+#define SIG(a_, b_) (((a_) >= (b_)) ? So[(int64_t)((a_) - (b_)) * ld + (b_) * cs] : So[(int64_t)((b_) - (a_)) * ld + (a_) * cs])
             for (int q = dmax; q >= 1; --q) {
                 T s = T(0);
                 for (int t = dmax; t >= 1; --t) s = fma(LL(i + t, i) * rinv, SIG(i + t, i + q), s);
-                So[(int64_t)q * ld + i] = -s;
+                So[(int64_t)q * ld + (i) * cs] = -s;
             }
             T s = T(0);
-            for (int t = dmax; t >= 1; --t) s = fma(LL(i + t, i) * rinv, So[(int64_t)t * ld + i], s);
-            So[i] = rinv * rinv - s;
-            for (int q = dmax + 1; q <= l; ++q) So[(int64_t)q * ld + i] = T(0);
+            for (int t = dmax; t >= 1; --t) s = fma(LL(i + t, i) * rinv, So[(int64_t)t * ld + (i) * cs], s);
+            So[i * cs] = rinv * rinv - s;
+            for (int q = dmax + 1; q <= l; ++q) So[(int64_t)q * ld + (i) * cs] = T(0);
 #undef SIG
         }
         if (ALG2) {
@@ -771,7 +803,7 @@ __device__ void run_bwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
             T *W = A.scratch2 + c.band;
             const T *Lbi = A.Lbar_in + c.band;
             T *Qo = A.Qbar + c.band;
-            for (int d = 0; d <= dmax; ++d) W[(int64_t)d * ld + j] = Lbi[(int64_t)d * ld + j] + (d >= 1 ? Pp[(int64_t)d * ld + j] : T(0));
+            for (int d = 0; d <= dmax; ++d) W[(int64_t)d * ld + (j) * cs] = Lbi[(int64_t)d * ld + (j) * cs] + (d >= 1 ? Pp[(int64_t)d * ld + (j) * cs] : T(0));
             if (OUTER) {
                 const T *Yb = A.Ybar + c.rhs;
                 const T *Xi = A.Xin + c.rhs;
@@ -779,36 +811,36 @@ __device__ void run_bwd_generic(const PlanDev &P, const SweepArgs<T> &A, const C
                 for (int r = 0; r < K; ++r) {
                     int64_t co = (int64_t)(A.rhs0 + r) * c.ldr;
                     T y = T(0);
-                    for (int d = 0; d <= dmax; ++d) y = fma(LL(j + d, j), Xi[co + j + d], y);
-                    const T ybar = Yb[co + j];
+                    for (int d = 0; d <= dmax; ++d) y = fma(LL(j + d, j), Xi[co + (j + d) * cs], y);
+                    const T ybar = Yb[co + (j) * cs];
                     for (int d = 0; d <= dmax; ++d) {
-                        T v = W[(int64_t)d * ld + j];
-                        v = fma(-Xi[co + j + d], ybar, v);
-                        v = fma(-Bb[co + j + d], y, v);
-                        W[(int64_t)d * ld + j] = v;
+                        T v = W[(int64_t)d * ld + (j) * cs];
+                        v = fma(-Xi[co + (j + d) * cs], ybar, v);
+                        v = fma(-Bb[co + (j + d) * cs], y, v);
+                        W[(int64_t)d * ld + (j) * cs] = v;
                     }
                 }
             }
-            if (A.ldbar) W[j] = W[j] + T(2.0 * A.ldbar[c.inst]) * rinv;
-            T lb0 = W[j];
+            if (A.ldbar) W[j * cs] = W[j * cs] + T(2.0 * A.ldbar[c.inst]) * rinv;
+            T lb0 = W[j * cs];
             for (int d = 1; d <= dmax; ++d) {
-                T qb = W[(int64_t)d * ld + j] * rinv;
-                W[(int64_t)d * ld + j] = qb;
+                T qb = W[(int64_t)d * ld + (j) * cs] * rinv;
+                W[(int64_t)d * ld + (j) * cs] = qb;
                 lb0 = fma(-qb, LL(j + d, j), lb0);
             }
-            W[j] = T(0.5) * lb0 * rinv;
+            W[j * cs] = T(0.5) * lb0 * rinv;
             for (int d = 0; d <= l; ++d) {
-                T *p = &Qo[(int64_t)d * ld + j];
-                *p = (d <= dmax) ? (A.acc ? (*p + W[(int64_t)d * ld + j]) : W[(int64_t)d * ld + j]) : T(0);
+                T *p = &Qo[(int64_t)d * ld + (j) * cs];
+                *p = (d <= dmax) ? (A.acc ? (*p + W[(int64_t)d * ld + (j) * cs]) : W[(int64_t)d * ld + (j) * cs]) : T(0);
             }
             for (int d = 0; d <= dmax; ++d) {
-                const T qb = W[(int64_t)d * ld + j];
+                const T qb = W[(int64_t)d * ld + (j) * cs];
                 for (int64_t m = imax64(j + d - l, 0); m < j; ++m) {
                     if (d == 0) {
-                        Pp[(int64_t)(j - m) * ld + m] = fma(T(-2) * qb, LL(j, m), Pp[(int64_t)(j - m) * ld + m]);
+                        Pp[(int64_t)(j - m) * ld + (m) * cs] = fma(T(-2) * qb, LL(j, m), Pp[(int64_t)(j - m) * ld + (m) * cs]);
                     } else {
-                        Pp[(int64_t)(j + d - m) * ld + m] = fma(-qb, LL(j, m), Pp[(int64_t)(j + d - m) * ld + m]);
-                        Pp[(int64_t)(j - m) * ld + m] = fma(-qb, LL(j + d, m), Pp[(int64_t)(j - m) * ld + m]);
+                        Pp[(int64_t)(j + d - m) * ld + (m) * cs] = fma(-qb, LL(j, m), Pp[(int64_t)(j + d - m) * ld + (m) * cs]);
+                        Pp[(int64_t)(j - m) * ld + (m) * cs] = fma(-qb, LL(j + d, m), Pp[(int64_t)(j - m) * ld + (m) * cs]);
                     }
                 }
             }

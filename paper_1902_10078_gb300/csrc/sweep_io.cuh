@@ -64,6 +64,8 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+template <typename T> struct SweepArgs;
+
 // ---------------------------------------------------------------------------
 // Pool pointers of one chain (instance offsets applied).
 // ---------------------------------------------------------------------------
@@ -72,6 +74,7 @@ struct ChainPtrs {
     const T *in[7];
     T *out[5];
     int64_t ld, ldr, n, rhs0;
+    int64_t cs;     // column stride (1: contiguous rows; 32: panel lanes)
     int acc;
     int kk;         // active RHS columns of this launch
 
@@ -97,6 +100,7 @@ struct DirectIO {
     const ChainPtrs<T> &P;
     __device__ DirectIO(const ChainPtrs<T> &p) : P(p) {}
     static constexpr int TW = 1;
+    static constexpr bool kWarpUniform = false;
     __device__ void begin_tiles(int64_t, int64_t, int64_t) {}
     __device__ __forceinline__ void tile_begin(int64_t) {}
     __device__ __forceinline__ void tile_end(int64_t, bool) {}
@@ -104,12 +108,12 @@ struct DirectIO {
         const StreamSpec s = SW::in_spec(S);
         const int64_t c = j + s.off;
         if (c < 0 || c >= P.n || !P.active(s)) return T(0);
-        return P.in_row(s)[c];
+        return P.in_row(s)[c * P.cs];
     }
     __device__ __forceinline__ void out(int O, int64_t j, int, T v) {
         const StreamSpec s = SW::out_spec(O);
         if (!P.active(s)) return;
-        T *p = P.out_row(s) + j;
+        T *p = P.out_row(s) + j * P.cs;
         const bool corner = !is_rhs_pool(s.pool) && (j + s.row >= P.n);
         *p = corner ? T(0) : (P.acc ? (*p + v) : v);
     }
@@ -135,6 +139,7 @@ struct StagedIO {
     static constexpr int NOUT = SW::NOUT;
     static constexpr int TW = 16 / (int)sizeof(T);     // columns per tile (one 16-byte chunk)
     static constexpr int RL = R + 1;                    // slots of a lagged stream
+    static constexpr bool kWarpUniform = false;
 
     __host__ __device__ static constexpr int off_of(int S) { return SW::in_spec(S).off; }
     __host__ __device__ static constexpr bool lagged(int S) { return (off_of(S) % TW) != 0; }
@@ -260,6 +265,124 @@ struct StagedIO {
         }
     }
 
+    __device__ void finish() { cp_async_wait<0>(); }
+};
+
+// ---------------------------------------------------------------------------
+// PanelIO (panel plans: 32 instances interleaved per column, cs = 32)
+//
+// The warp's lanes are lanes 0..31 of one instance group at the same segment,
+// so column c of a stream row is 32 adjacent elements and TW consecutive
+// columns are one contiguous block of TW * 32 elements.  Inputs go through a
+// per-warp ring [stream][slot][u][lane]: the warp copies each block with
+// 16-byte cp.async, every lane a 16-byte piece, whatever the stream's column
+// offset (a row shift of whole 32-element columns), and each lane reads its
+// own column u with a bank-conflict-free shared load.  Outputs need no
+// staging: every lane stores its element of column j, and the warp's stores
+// of one column form one contiguous run.  The loop over tiles is uniform over
+// the warp (the copies are cooperative); lanes outside their own rows skip
+// the steps.
+// ---------------------------------------------------------------------------
+template <typename T, class SW, int R, int DIR>
+struct PanelIO {
+    static constexpr int NIN = SW::NIN;
+    static constexpr int NOUT = SW::NOUT;
+    static constexpr int TW = 4;                                     // columns per tile
+    static constexpr int kTileElems = TW * kWarp;
+    static constexpr int kPieces = kTileElems * (int)sizeof(T) / (16 * kWarp);   // 16-byte pieces per lane
+    static constexpr int kPieceElems = 16 / (int)sizeof(T);
+    static constexpr int kRingElems = NIN * R * kTileElems;
+    static constexpr int kWarpElems = kRingElems;
+    static constexpr bool kWarpUniform = true;
+    static_assert(kPieces >= 1, "a tile must give every lane at least one 16-byte piece");
+
+    const ChainPtrs<T> &P;          // this lane's pools (outputs)
+    const SweepArgs<T> &A;          // pool bases (inputs, addressed by the group)
+    const Task &G;                  // group geometry
+    T *ring;                        // the warp's ring
+    int lane;
+    int cR, iR;                     // ring slots of the current row tile and of the next one to issue
+    const T *cur;                   // this lane's column in the current slot
+
+    __device__ PanelIO(const ChainPtrs<T> &p, const SweepArgs<T> &a, const Task &g, T *warp_smem, int lane_)
+        : P(p), A(a), G(g), ring(warp_smem), lane(lane_) {}
+
+    __device__ static __forceinline__ int wrap_add(int x, int d) {
+        x += d;
+        return x >= R ? x - R : (x < 0 ? x + R : x);
+    }
+
+    // Row `s.row` of the stream's pool for lane 0 of the group.
+    __device__ __forceinline__ const T *group_row(const StreamSpec &s) const {
+        const T *base = nullptr;
+        switch (s.pool) {
+            case POOL_Q: base = A.Q; break;
+            case POOL_LIN: base = A.Lin; break;
+            case POOL_S: base = A.S; break;
+            case POOL_SBAR: base = A.Sbar; break;
+            case POOL_LBARIN: base = A.Lbar_in; break;
+            case POOL_BIN: base = A.Bin; break;
+            default: base = A.Xin; break;
+        }
+        if (is_rhs_pool(s.pool)) return base + G.grhs + (int64_t)(P.rhs0 + s.row) * G.gldr;
+        return base + G.gband + (int64_t)s.row * G.gld;
+    }
+
+    // Copy into slot q the block of stream S for row tile m: columns
+    // m TW + off .. + TW - 1 of all 32 lanes.  Columns outside [0, gn) are
+    // zero filled, not read.
+    __device__ __forceinline__ void issue(int S, int64_t m, int q) {
+        const StreamSpec s = SW::in_spec(S);
+        const int64_t c0 = m * TW + s.off;
+        const bool act = P.active(s);
+        const T *row = group_row(s);
+        T *dst = ring + (S * R + q) * kTileElems;
+#pragma unroll
+        for (int t = 0; t < kPieces; ++t) {
+            const int e = (lane + kWarp * t) * kPieceElems;        // element offset inside the block
+            const int64_t c = c0 + e / kWarp;
+            const bool valid = act && c >= 0 && c < G.gn;
+            // an invalid piece reads nothing (source size 0): the address is only a placeholder
+            cp_async16(dst + e, valid ? row + c0 * kWarp + e : row, valid);
+        }
+    }
+    __device__ __forceinline__ void issue_all(int64_t m, int q) {
+#pragma unroll
+        for (int S = 0; S < NIN; ++S) issue(S, m, q);
+    }
+
+    __device__ void begin_tiles(int64_t m0, int64_t, int64_t) {
+        cR = (int)(((m0 % R) + R) % R);
+        iR = cR;
+        for (int t = 0; t < R - 1; ++t) {
+            issue_all(m0 + DIR * t, iR);
+            cp_async_commit();
+            iR = wrap_add(iR, DIR);
+        }
+    }
+
+    __device__ __forceinline__ void tile_begin(int64_t m) {
+        __syncwarp();                      // every lane is done with the slot about to be refilled
+        issue_all(m + DIR * (R - 1), iR);
+        cp_async_commit();
+        iR = wrap_add(iR, DIR);
+        cp_async_wait<R - 1>();
+        __syncwarp();                      // the other lanes' pieces of tile m have landed
+        cur = ring + cR * kTileElems + lane;
+        cR = wrap_add(cR, DIR);
+    }
+
+    __device__ __forceinline__ T in(int S, int64_t, int u) const { return cur[S * R * kTileElems + u * kWarp]; }
+
+    __device__ __forceinline__ void out(int O, int64_t j, int, T v) {
+        const StreamSpec s = SW::out_spec(O);
+        if (!P.active(s)) return;
+        T *p = P.out_row(s) + j * P.cs;
+        const bool corner = !is_rhs_pool(s.pool) && (j + s.row >= P.n);
+        *p = corner ? T(0) : (P.acc ? (*p + v) : v);
+    }
+
+    __device__ __forceinline__ void tile_end(int64_t, bool) {}
     __device__ void finish() { cp_async_wait<0>(); }
 };
 

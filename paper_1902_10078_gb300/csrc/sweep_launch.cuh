@@ -73,7 +73,7 @@ __device__ __forceinline__ int state_words(int l) {
 __device__ __forceinline__ ChainCtx make_ctx(const PlanDev &P, int32_t inst, int32_t seg) {
     const InstDev I = P.inst[inst];
     ChainCtx c;
-    c.n = I.n; c.band = I.band; c.ld = I.ld; c.rhs = I.rhs; c.ldr = I.ldr; c.l = I.l;
+    c.n = I.n; c.band = I.band; c.ld = I.ld; c.rhs = I.rhs; c.ldr = I.ldr; c.cs = I.cs; c.l = I.l;
     c.inst = inst;
     c.warm = I.warm;
     c.gseg = I.seg0 + seg;
@@ -84,34 +84,57 @@ __device__ __forceinline__ ChainCtx make_ctx(const PlanDev &P, int32_t inst, int
     return c;
 }
 
+// Context of an idle lane of a panel task: no rows, nothing written.
+__device__ __forceinline__ ChainCtx idle_ctx() {
+    ChainCtx c;
+    c.n = 0; c.band = 0; c.ld = 0; c.rhs = 0; c.ldr = 0; c.cs = kPanelLanes; c.l = 0;
+    c.inst = -1; c.warm = 0; c.gseg = 0; c.a = 0; c.b = 0;
+    c.first = true; c.last = true;
+    return c;
+}
+
 // ---------------------------------------------------------------------------
 // Staged kernel for one bandwidth L: block b runs warp tasks
 // [task0 + WPB b, task0 + WPB (b+1)) of the bandwidth's task range (ordered
-// longest first); each lane runs one chain through its shared-memory rings.
+// longest first); each lane runs one chain.  Row plans stage every lane's own
+// rows (StagedIO); panel plans stage the group's interleaved columns with the
+// whole warp (PanelIO), so idle lanes stay in the loop.
 // ---------------------------------------------------------------------------
-template <typename T, int L, int K, int FL, bool FWD>
+template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
+struct StagedIOOf {
+    using SW = typename SweepOf<T, L, K, FL, FWD>::type;
+    using type = typename std::conditional<PANEL, PanelIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>,
+                                           StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>>::type;
+};
+
+template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
 __global__ void __launch_bounds__(kWarp * kStagedWarpsPerBlock)
 staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
-    using SW = typename SweepOf<T, L, K, FL, FWD>::type;
-    using IO = StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>;
+    using IO = typename StagedIOOf<T, L, K, FL, FWD, PANEL>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     const int t = blockIdx.x * kStagedWarpsPerBlock + warp;
     if (t >= ntasks) return;
     const Task task = P.tasks[task0 + t];
     const Chain ch = P.chains[(int64_t)task.chain0 + lane];
-    if (ch.inst < 0) return;
-    const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
-    const ChainPtrs<T> ptrs = chain_ptrs(A, c);
     T *wsm = reinterpret_cast<T *>(smem_raw) + (size_t)warp * IO::kWarpElems;
-    IO io(ptrs, wsm, lane);
-    run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
+    if constexpr (PANEL) {
+        const ChainCtx c = ch.inst >= 0 ? make_ctx(P, ch.inst, ch.seg) : idle_ctx();
+        const ChainPtrs<T> ptrs = chain_ptrs(A, c);
+        IO io(ptrs, A, task, wsm, lane);
+        run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
+    } else {
+        if (ch.inst < 0) return;
+        const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
+        const ChainPtrs<T> ptrs = chain_ptrs(A, c);
+        IO io(ptrs, wsm, lane);
+        run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
+    }
 }
 
-template <typename T, int L, int K, int FL, bool FWD>
+template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
 constexpr size_t staged_smem_bytes() {
-    using SW = typename SweepOf<T, L, K, FL, FWD>::type;
-    return sizeof(T) * (size_t)StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>::kWarpElems * kStagedWarpsPerBlock;
+    return sizeof(T) * (size_t)StagedIOOf<T, L, K, FL, FWD, PANEL>::type::kWarpElems * kStagedWarpsPerBlock;
 }
 
 // ---------------------------------------------------------------------------
@@ -138,50 +161,78 @@ __global__ void __launch_bounds__(128) sweep_kernel(PlanDev P, SweepArgs<T> A, i
 }
 
 // ---------------------------------------------------------------------------
-// Verify / fixup: one thread per segmented instance walks its segment
-// boundaries in sweep order.  A segment whose cold-started state differs
-// (bitwise) from its predecessor's exact end state is rerun from that exact
-// state, which rewrites its outputs and its own end state.  Forward sweeps
-// that compute the Cholesky then reduce the per-segment log-det and info.
+// Verify / fixup: one warp per segmented instance.  The lanes compare the
+// segment boundaries in parallel; from the first boundary (in sweep order)
+// whose cold-started state differs bitwise from its predecessor's exact end
+// state, lane 0 reruns segments from the exact state, one after the other,
+// as long as the rerun changes the next boundary.  Forward Cholesky sweeps
+// then reduce the per-segment log-det (a fixed tree over the lanes) and info.
 // ---------------------------------------------------------------------------
+constexpr int kVerifyWarps = 4;
+
 template <typename T, int K, int FL, bool FWD>
-__global__ void __launch_bounds__(64) verify_kernel(PlanDev P, SweepArgs<T> A) {
-    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kWarp * kVerifyWarps) verify_kernel(PlanDev P, SweepArgs<T> A) {
+    const int inst = blockIdx.x * kVerifyWarps + threadIdx.x / kWarp;
+    const int lane = threadIdx.x % kWarp;
     if (inst >= P.count) return;
     const InstDev I = P.inst[inst];
     if (I.nseg <= 1) return;
     const int words = state_words<T, K, FL, FWD>(I.l);
+    // boundary b (1 <= b < nseg) joins segments b-1 and b; in sweep order the
+    // forward sweeps meet them ascending, the backward sweeps descending
+    auto boundary_ok = [&](int b) {
+        const int64_t g = I.seg0 + b;
+        return FWD ? snap_equal(snap_ptr<T>(P, g - 1, 1), (const T *)snap_ptr<T>(P, g, 0), words)
+                   : snap_equal(snap_ptr<T>(P, g, 1), (const T *)snap_ptr<T>(P, g - 1, 0), words);
+    };
+    int first = FWD ? I.nseg : 0;          // first failing boundary in sweep order (none: past the end)
+    for (int b = 1 + lane; b < I.nseg; b += kWarp)
+        if (!boundary_ok(b)) first = FWD ? min(first, b) : max(first, b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int v = __shfl_xor_sync(0xffffffffu, first, o);
+        first = FWD ? min(first, v) : max(first, v);
+    }
     unsigned int fixes = 0;
-    if (FWD) {
-        for (int p = 1; p < I.nseg; ++p) {
-            const int64_t g = I.seg0 + p;
-            const T *prev_end = snap_ptr<T>(P, g - 1, 1);
-            if (!snap_equal(prev_end, (const T *)snap_ptr<T>(P, g, 0), words)) {
-                run_chain_direct<T, K, FL, FWD>(P, A, make_ctx(P, inst, p), RUN_EXACT, prev_end);
+    if (lane == 0) {
+        // from the first failure on, walk the boundaries in sweep order: a rerun rewrites the
+        // segment's end state, which the next boundary then compares against
+        if (FWD) {
+            for (int b = first; b < I.nseg; ++b) {
+                if (b > first && boundary_ok(b)) continue;
+                run_chain_direct<T, K, FL, FWD>(P, A, make_ctx(P, inst, b), RUN_EXACT,
+                                                snap_ptr<T>(P, I.seg0 + b - 1, 1));
                 ++fixes;
             }
-        }
-    } else {
-        for (int p = I.nseg - 2; p >= 0; --p) {
-            const int64_t g = I.seg0 + p;
-            const T *next_end = snap_ptr<T>(P, g + 1, 1);
-            if (!snap_equal(next_end, (const T *)snap_ptr<T>(P, g, 0), words)) {
-                run_chain_direct<T, K, FL, FWD>(P, A, make_ctx(P, inst, p), RUN_EXACT, next_end);
+        } else {
+            for (int b = first; b >= 1; --b) {
+                if (b < first && boundary_ok(b)) continue;
+                run_chain_direct<T, K, FL, FWD>(P, A, make_ctx(P, inst, b - 1), RUN_EXACT,
+                                                snap_ptr<T>(P, I.seg0 + b, 1));
                 ++fixes;
             }
         }
     }
+    __syncwarp();
     if constexpr (FWD && (FL & F_CHOL)) {
         double ld = 0.0;
-        int32_t info = 0;
-        for (int p = 0; p < I.nseg; ++p) {
+        int bad = I.nseg;                  // first segment with a failed pivot
+        for (int p = lane; p < I.nseg; p += kWarp) {
             ld += P.seg_logdet[I.seg0 + p];
-            if (info == 0) info = P.seg_info[I.seg0 + p];
+            if (P.seg_info[I.seg0 + p] != 0) bad = min(bad, p);
         }
-        if (A.logdet) A.logdet[inst] = info ? (double)NAN : ld;
-        A.info[inst] = info;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ld += __shfl_xor_sync(0xffffffffu, ld, o);
+            bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+        }
+        if (lane == 0) {
+            const int32_t info = bad < I.nseg ? P.seg_info[I.seg0 + bad] : 0;
+            if (A.logdet) A.logdet[inst] = info ? (double)NAN : ld;
+            A.info[inst] = info;
+        }
     }
-    if (fixes) atomicAdd(P.counters + kNumSweepKinds + A.kind, fixes);
+    if (lane == 0 && fixes) atomicAdd(P.counters + kNumSweepKinds + A.kind, fixes);
 }
 
 // ---------------------------------------------------------------------------
@@ -196,21 +247,27 @@ inline bool args_aligned16(const SweepArgs<T> &A) {
            aligned16(A.Bin) && aligned16(A.Xout) && aligned16(A.Xin) && aligned16(A.Ybar);
 }
 
-template <typename T, int L, int K, int FL, bool FWD>
-static cudaError_t launch_staged_l(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
+template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
+static cudaError_t launch_staged_lp(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
     const int32_t t0 = p->class_task0[L], nt = p->class_task0[L + 1] - t0;
     if (nt <= 0) return cudaSuccess;
-    constexpr size_t smem = staged_smem_bytes<T, L, K, FL, FWD>();
+    constexpr size_t smem = staged_smem_bytes<T, L, K, FL, FWD, PANEL>();
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(staged_kernel<T, L, K, FL, FWD>,
+        cudaError_t e = cudaFuncSetAttribute(staged_kernel<T, L, K, FL, FWD, PANEL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const unsigned blocks = (unsigned)((nt + kStagedWarpsPerBlock - 1) / kStagedWarpsPerBlock);
-    staged_kernel<T, L, K, FL, FWD><<<blocks, kWarp * kStagedWarpsPerBlock, smem, s>>>(p->dev, A, t0, nt);
+    staged_kernel<T, L, K, FL, FWD, PANEL><<<blocks, kWarp * kStagedWarpsPerBlock, smem, s>>>(p->dev, A, t0, nt);
     return cudaGetLastError();
+}
+
+template <typename T, int L, int K, int FL, bool FWD>
+static cudaError_t launch_staged_l(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
+    return p->layout == kLayoutPanels ? launch_staged_lp<T, L, K, FL, FWD, true>(p, A, s)
+                                      : launch_staged_lp<T, L, K, FL, FWD, false>(p, A, s);
 }
 
 template <typename T, int K, int FL, bool FWD>
@@ -240,7 +297,7 @@ static cudaError_t launch_direct(const bnd_plan *p, const SweepArgs<T> &A, int32
 template <typename T, int K, int FL, bool FWD>
 static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    const bool staged = p->staged_ok && args_aligned16(A) && !p->force_direct;
+    const bool staged = p->layout != kLayoutStrided && p->staged_ok && args_aligned16(A) && !p->force_direct;
     if (!staged) {
         e = launch_direct<T, K, FL, FWD>(p, A, 0, p->ntasks, s);
     } else {
@@ -268,7 +325,8 @@ static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cuda
     }
     if (e != cudaSuccess) return e;
     if (p->nsegs > p->count) {
-        verify_kernel<T, K, FL, FWD><<<(p->count + 63) / 64, 64, 0, s>>>(p->dev, A);
+        verify_kernel<T, K, FL, FWD><<<(p->count + kVerifyWarps - 1) / kVerifyWarps, kWarp * kVerifyWarps, 0, s>>>(
+            p->dev, A);
         e = cudaGetLastError();
     }
     return e;

@@ -18,8 +18,8 @@ def symmetric_weights(layout, device="cuda"):
     """Band pool with 1 on the diagonal row, 2 on the off-diagonal rows, 0 at corners/padding."""
     w = torch.zeros(layout.band_elems, dtype=torch.float64)
     for i in range(layout.count):
-        n, l, ld, o = layout.ns[i], layout.ls[i], layout.ld[i], layout.band_off[i]
-        v = w[o:o + layout.rows[i] * ld].view(layout.rows[i], ld)
+        n, l = layout.ns[i], layout.ls[i]
+        v = layout.band_view(w, i)
         v[0, :n] = 1.0
         for d in range(1, min(l, n - 1) + 1):
             v[d, : n - d] = 2.0

@@ -100,3 +100,62 @@ def test_many_tasks_for_many_instances(lib):
         assert B.bnd_plan_tasks(p) == 5          # 20 instances per bandwidth -> one task each
     finally:
         B.bnd_plan_destroy(p)
+
+
+def _panel_insts(ns, ls, k=1):
+    from paper_1902_10078_gb300 import batch as BT
+    return BT.Layout(ns, ls, k, B.BND_F32, panels=True).insts()
+
+
+def test_plan_recognises_rows_and_panels(lib):
+    p = B.bnd_plan_create(B.BND_F32, _insts([100, 200], [2, 3]), 1)
+    try:
+        assert B.bnd_plan_layout(p) == B.LAYOUT_ROWS
+    finally:
+        B.bnd_plan_destroy(p)
+    p = B.bnd_plan_create(B.BND_F32, _panel_insts([100, 200, 50], [2, 2, 3]), 1)
+    try:
+        assert B.bnd_plan_layout(p) == B.LAYOUT_PANELS
+    finally:
+        B.bnd_plan_destroy(p)
+
+
+def test_panel_tasks_follow_groups(lib):
+    # 40 instances of l = 3 -> groups of 32 and 8 lanes; the group's longest n (5000) sets the
+    # segment length (1024 -> round(5000 / 1024) = 5 segments of 1000 rows); one task per
+    # (group, segment), lanes past their own end idle
+    ns = sorted([5000 - 10 * i for i in range(40)], reverse=True)
+    ins = _panel_insts(ns, [3] * 40)
+    p = B.bnd_plan_create(B.BND_F32, ins, 1, dict(seg_len=1024, warmup=64))
+    try:
+        assert B.bnd_plan_layout(p) == B.LAYOUT_PANELS
+        assert B.bnd_plan_tasks(p) == 5 + 5
+        assert B.bnd_plan_chains(p) == sum((n + 999) // 1000 for n in ns)
+    finally:
+        B.bnd_plan_destroy(p)
+
+
+def test_panel_groups_break_on_bandwidth_and_offsets(lib):
+    ins = _panel_insts([100] * 5 + [90] * 3, [2] * 5 + [4] * 3)
+    p = B.bnd_plan_create(B.BND_F32, ins, 1, dict(seg_len=-1))
+    try:
+        assert B.bnd_plan_layout(p) == B.LAYOUT_PANELS
+        assert B.bnd_plan_tasks(p) == 2          # one task per group
+    finally:
+        B.bnd_plan_destroy(p)
+    # a column stride other than 1 or 32 (or ld not a multiple of 32) is a general strided batch
+    odd = [dict(n=10, l=2, band=0, ld=40, rhs=0, ldr=40, cs=4)]
+    p = B.bnd_plan_create(B.BND_F32, odd, 1)
+    try:
+        assert B.bnd_plan_layout(p) == B.LAYOUT_STRIDED
+    finally:
+        B.bnd_plan_destroy(p)
+
+
+@pytest.mark.parametrize("bad", [dict(cs=-1), dict(cs=32, ld=32 * 9), dict(cs=2, ld=19)])
+def test_plan_rejects_bad_strides(lib, bad):
+    d = dict(n=10, l=2, band=0, ld=400, rhs=0, ldr=400)
+    d.update(bad)
+    with pytest.raises(B.BandedError) as e:
+        B.bnd_plan_create(B.BND_F32, [d], 1)
+    assert e.value.status == 1

@@ -1,17 +1,19 @@
 """GPU parity: every operator of the C ABI against the FP64 oracle.
 
 Inputs are seeded synthetic SPD bands (workloads.py), rounded to the tested
-dtype before both sides see them.  Batches mix bandwidths 1..8, ragged n
+dtype before both sides see them.  Batches mix bandwidths 0..12, ragged n
 (1, 2, 3, 5, 17, ... 4100) and run both as whole chains and split into
 segments (speculative starts + verify/fixup), so several tiles, segment
-boundaries and ragged tails are covered.
+boundaries and ragged tails are covered.  Every operator runs on both pool
+arrangements: contiguous rows (cs = 1) and 32-lane panels (cs = 32), the
+latter with full, partial and single-lane groups.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle as O
-from gpu_helpers import MIXED, TOL, assert_close, dev, rounded, setup, sync
+from gpu_helpers import ARRANGEMENTS, TOL, assert_close, dev, rounded, setup, shapes_for, sync
 from paper_1902_10078_gb300 import binding as B
 from paper_1902_10078_gb300.workloads import zero_corners
 
@@ -33,10 +35,11 @@ def oracle_L(insts, dtype):
     return [rounded(O.cholesky(i.Q)[0], dtype) for i in insts]
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("tune", list(TUNINGS))
-def test_cholesky_and_logdet(dtype, tune):
-    insts, lay, plan = setup(MIXED, 1, dtype, TUNINGS[tune])
+def test_cholesky_and_logdet(dtype, tune, arr):
+    insts, lay, plan = setup(shapes_for(arr), 1, dtype, TUNINGS[tune], arr=arr)
     Q = dev(lay, lay.pack_band([i.Q for i in insts]))
     L = lay.band_pool(fill=7.0)
     logdet = torch.empty(lay.count, dtype=torch.float64, device="cuda")
@@ -53,12 +56,13 @@ def test_cholesky_and_logdet(dtype, tune):
         assert abs(float(logdet[c]) - ld) <= tol["logdet"] * max(1.0, abs(ld))
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("tune", list(TUNINGS))
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("k", [1, 3, 6])
-def test_solve(dtype, tune, mode, k):
-    insts, lay, plan = setup(MIXED, k, dtype, TUNINGS[tune])
+def test_solve(dtype, tune, mode, k, arr):
+    insts, lay, plan = setup(shapes_for(arr), k, dtype, TUNINGS[tune], arr=arr)
     Ls = oracle_L(insts, dtype)
     L = dev(lay, lay.pack_band(Ls))
     Bp = dev(lay, lay.pack_rhs([i.B for i in insts]))
@@ -71,10 +75,11 @@ def test_solve(dtype, tune, mode, k):
         assert_close(f"X[{c}]", Xg[c], ref, TOL[dtype]["fwd"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("tune", list(TUNINGS))
-def test_subset_inverse(dtype, tune):
-    insts, lay, plan = setup(MIXED, 1, dtype, TUNINGS[tune])
+def test_subset_inverse(dtype, tune, arr):
+    insts, lay, plan = setup(shapes_for(arr), 1, dtype, TUNINGS[tune], arr=arr)
     Ls = oracle_L(insts, dtype)
     L = dev(lay, lay.pack_band(Ls))
     S = lay.band_pool(fill=5.0)
@@ -85,11 +90,12 @@ def test_subset_inverse(dtype, tune):
         assert_close(f"S[{c}]", Sg[c], O.subset_inverse(Ls[c]), TOL[dtype]["fwd"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("tune", list(TUNINGS))
 @pytest.mark.parametrize("acc", [0, 1])
-def test_cholesky_vjp(dtype, tune, acc):
-    insts, lay, plan = setup(MIXED, 1, dtype, TUNINGS[tune])
+def test_cholesky_vjp(dtype, tune, acc, arr):
+    insts, lay, plan = setup(shapes_for(arr), 1, dtype, TUNINGS[tune], arr=arr)
     Ls = oracle_L(insts, dtype)
     rng = np.random.Generator(np.random.PCG64(5))
     Lbars = [zero_corners(rounded(rng.normal(size=L.shape), dtype)) for L in Ls]
@@ -111,11 +117,12 @@ def test_cholesky_vjp(dtype, tune, acc):
         assert_close(f"Qbar[{c}]", Qg[c], ref, TOL[dtype]["grad"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("tune", list(TUNINGS))
 @pytest.mark.parametrize("acc", [0, 1])
-def test_subset_inverse_vjp(dtype, tune, acc):
-    insts, lay, plan = setup(MIXED, 1, dtype, TUNINGS[tune])
+def test_subset_inverse_vjp(dtype, tune, acc, arr):
+    insts, lay, plan = setup(shapes_for(arr), 1, dtype, TUNINGS[tune], arr=arr)
     Ls = oracle_L(insts, dtype)
     Ss = [rounded(O.subset_inverse(L), dtype) for L in Ls]
     rng = np.random.Generator(np.random.PCG64(6))
@@ -134,11 +141,12 @@ def test_subset_inverse_vjp(dtype, tune, acc):
         assert_close(f"Lbar[{c}]", Lg[c], ref, TOL[dtype]["grad"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("k", [1, 4])
-def test_solve_vjp(dtype, mode, k):
-    insts, lay, plan = setup(MIXED, k, dtype, TUNINGS["seg"])
+def test_solve_vjp(dtype, mode, k, arr):
+    insts, lay, plan = setup(shapes_for(arr), k, dtype, TUNINGS["seg"], arr=arr)
     Ls = oracle_L(insts, dtype)
     refs_X, refs_Bb, refs_Lb = [], [], []
     for c, ins in enumerate(insts):
@@ -168,11 +176,12 @@ def test_solve_vjp(dtype, mode, k):
         assert_close(f"Lbar[{c}]", Lg[c], refs_Lb[c], TOL[dtype]["grad"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("tune", list(TUNINGS))
 @pytest.mark.parametrize("k", [1, 2, 4])
-def test_fused_gmm_step(dtype, tune, k):
-    insts, lay, plan = setup(MIXED, k, dtype, TUNINGS[tune])
+def test_fused_gmm_step(dtype, tune, k, arr):
+    insts, lay, plan = setup(shapes_for(arr), k, dtype, TUNINGS[tune], arr=arr)
     res, _ = O.batch_step(insts)
     Q = dev(lay, lay.pack_band([i.Q for i in insts]))
     Bp = dev(lay, lay.pack_rhs([i.B for i in insts]))
@@ -204,13 +213,14 @@ PROD = [((2, 0), 0, (2, 0), 1, (2, 2)), ((2, 0), 0, (2, 0), 1, (2, 0)), ((3, 0),
         ((1, 2), 0, (2, 1), 0, (3, 3)), ((1, 2), 1, (0, 3), 1, (1, 1)), ((3, 1), 0, (2, 2), 1, (6, 2))]
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("case", range(len(PROD)))
-def test_products(dtype, case):
+def test_products(dtype, case, arr):
     from test_oracle_pins import rand_general
     (alo, aup), ta, (blo, bup), tb, (clo, cup) = PROD[case]
     shapes = [(n, 8) for n in (1, 2, 7, 300, 1500)]        # 9 rows per instance: room for every operand
-    insts, lay, plan = setup(shapes, 2, dtype, TUNINGS["whole"])
+    insts, lay, plan = setup(shapes, 2, dtype, TUNINGS["whole"], arr=arr)
     As = [rounded(rand_general(n, alo, aup, 10 + i), dtype) for i, (n, _) in enumerate(shapes)]
     Bs = [rounded(rand_general(n, blo, bup, 20 + i), dtype) for i, (n, _) in enumerate(shapes)]
     Cbs = [rounded(rand_general(n, clo, cup, 30 + i), dtype) for i, (n, _) in enumerate(shapes)]
@@ -229,11 +239,12 @@ def test_products(dtype, case):
         assert_close("Bbar", Bbg[c], rb, TOL[dtype]["grad"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_outer_and_matvec(dtype):
+def test_outer_and_matvec(dtype, arr):
     from test_oracle_pins import rand_general
     shapes = [(n, 8) for n in (1, 3, 50, 999)]
-    insts, lay, plan = setup(shapes, 3, dtype, TUNINGS["whole"])
+    insts, lay, plan = setup(shapes, 3, dtype, TUNINGS["whole"], arr=arr)
     rng = np.random.Generator(np.random.PCG64(3))
     Ms = [rounded(rng.normal(size=(3, n)), dtype) for n, _ in shapes]
     Vs = [rounded(rng.normal(size=(3, n)), dtype) for n, _ in shapes]

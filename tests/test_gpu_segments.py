@@ -16,13 +16,20 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_helpers import TOL, assert_close, dev, setup, sync
+from gpu_helpers import ARRANGEMENTS, TOL, assert_close, dev, setup, sync
 from paper_1902_10078_gb300 import binding as B
 from paper_1902_10078_gb300.workloads import zero_corners
 
 pytestmark = pytest.mark.gpu
 
 LONG = [(6000, 1), (5000, 3), (7001, 7), (4500, 2), (3333, 5), (300, 4), (4096, 8)]
+# panels: several lanes per group, lanes that end segments early or are idle in later ones
+LONG_PANELS = sorted([(6000, 1), (5900, 1), (100, 1), (5000, 3), (4999, 3), (7001, 7), (6000, 7), (3333, 5),
+                      (4096, 8), (4500, 2), (4000, 2), (300, 4), (1, 4)], key=lambda s: (s[1], -s[0]))
+
+
+def long_for(arr):
+    return LONG if arr == "rows" else LONG_PANELS
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,30 +38,34 @@ def _built():
     bld.build()
 
 
-def run_gmm(lay, plan, insts):
-    Q = dev(lay, lay.pack_band([i.Q for i in insts]))
-    Bp = dev(lay, lay.pack_rhs([i.B for i in insts]))
-    L, S, X = lay.band_pool(), lay.band_pool(), lay.rhs_pool()
+def run_gmm(lay, plan, insts, pad=0.0, out_fill=0.0):
+    """Fused forward + backward; `pad` fills the input pools outside the
+    instances, `out_fill` pre-fills the output pools."""
+    Q = dev(lay, lay.pack_band([i.Q for i in insts], fill=pad))
+    Bp = dev(lay, lay.pack_rhs([i.B for i in insts], fill=pad))
+    L, S, X = lay.band_pool(fill=out_fill), lay.band_pool(fill=out_fill), lay.rhs_pool(fill=out_fill)
     logdet = torch.empty(lay.count, dtype=torch.float64, device="cuda")
     info = torch.empty(lay.count, dtype=torch.int32, device="cuda")
     B.banded_gmm_forward(plan.handle, Q, Bp, L, X, S, logdet, info)
-    Xb = dev(lay, lay.pack_rhs([i.Xbar for i in insts]))
-    Sb = dev(lay, lay.pack_band([i.Sbar for i in insts]))
+    Xb = dev(lay, lay.pack_rhs([i.Xbar for i in insts], fill=pad))
+    Sb = dev(lay, lay.pack_band([i.Sbar for i in insts], fill=pad))
     ldb = torch.full((lay.count,), 0.5, dtype=torch.float64, device="cuda")
-    Qb, Bb = lay.band_pool(), lay.rhs_pool()
+    Qb, Bb = lay.band_pool(fill=out_fill), lay.rhs_pool(fill=out_fill)
     B.banded_gmm_backward(plan.handle, L, X, S, Xb, Sb, ldb, Qb, Bb)
     sync()
     return dict(L=L, S=S, X=X, Qb=Qb, Bb=Bb, logdet=logdet.cpu().numpy(), info=info.cpu().numpy())
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", [B.BND_F32, B.BND_F64])
 @pytest.mark.parametrize("warm", [0, 1])
 @pytest.mark.parametrize("flags", [0, 1])
-def test_segmented_is_bitwise_equal_to_whole(dtype, warm, flags):
+def test_segmented_is_bitwise_equal_to_whole(dtype, warm, flags, arr):
     # staged (flags 0) and direct (flags 1) kernels run the same arithmetic: bitwise equal to each other too
-    insts, lay, whole = setup(LONG, 4, dtype, dict(seg_len=-1, flags=1))
+    shapes = long_for(arr)
+    insts, lay, whole = setup(shapes, 4, dtype, dict(seg_len=-1, flags=1), arr=arr)
     ref = run_gmm(lay, whole, insts)
-    _, _, seg = setup(LONG, 4, dtype, dict(seg_len=512, warmup=warm, flags=flags))
+    _, _, seg = setup(shapes, 4, dtype, dict(seg_len=512, warmup=warm, flags=flags), arr=arr)
     assert seg.chains > lay.count
     got = run_gmm(lay, seg, insts)
     for key in ("L", "S", "X", "Qb", "Bb"):
@@ -67,10 +78,11 @@ def test_segmented_is_bitwise_equal_to_whole(dtype, warm, flags):
         assert sum(B.bnd_plan_fixups(seg.handle, kind) for kind in range(4)) > 0
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
-def test_degenerate_shapes(dtype):
+def test_degenerate_shapes(dtype, arr):
     shapes = [(1, 1), (1, 7), (2, 5), (3, 3), (4, 0), (40, 0), (50, 12), (23, 9), (200, 16), (8, 30)]
-    insts, lay, plan = setup(shapes, 2, dtype, dict(seg_len=-1))
+    insts, lay, plan = setup(shapes, 2, dtype, dict(seg_len=-1), arr=arr)
     got = run_gmm(lay, plan, insts)
     res, _ = O.batch_step(insts)
     tol = TOL[dtype]
@@ -86,10 +98,11 @@ def test_degenerate_shapes(dtype):
         assert abs(got["logdet"][c] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", [B.BND_F32, B.BND_F64])
-def test_corners_never_read_and_written_zero(dtype):
-    shapes = [(50, 3), (9, 7), (700, 5), (3000, 2)]
-    insts, lay, plan = setup(shapes, 1, dtype, dict(seg_len=256, warmup=64))
+def test_corners_never_read_and_written_zero(dtype, arr):
+    shapes = [(50, 3), (9, 3), (700, 5), (3000, 2), (2999, 2)]
+    insts, lay, plan = setup(shapes, 1, dtype, dict(seg_len=256, warmup=64), arr=arr)
     for ins in insts:
         zero_corners(ins.Q, fill=np.nan)
         zero_corners(ins.Sbar, fill=np.nan)
@@ -108,11 +121,12 @@ def test_corners_never_read_and_written_zero(dtype):
             assert_close(key, a, r[ref_key], TOL[dtype]["grad"])
 
 
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
 @pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
 @pytest.mark.parametrize("tune", [dict(seg_len=-1), dict(seg_len=128, warmup=32)])
-def test_not_spd_reports_info(dtype, tune):
-    shapes = [(600, 2), (800, 3), (500, 1)]
-    insts, lay, plan = setup(shapes, 1, dtype, tune)
+def test_not_spd_reports_info(dtype, tune, arr):
+    shapes = [(600, 3), (800, 3), (500, 3)]
+    insts, lay, plan = setup(shapes, 1, dtype, tune, arr=arr)
     insts[1].Q[0, 437] = -50.0          # instance 1 fails at row 437 at the latest
     Lo, inf = O.cholesky(insts[1].Q)
     assert inf > 0
@@ -132,3 +146,33 @@ def test_not_spd_reports_info(dtype, tune):
                  TOL[dtype]["fwd"])
     for c in (0, 2):
         assert_close("unaffected instance", Lg[c], O.cholesky(insts[c].Q)[0], TOL[dtype]["fwd"])
+
+
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
+@pytest.mark.parametrize("dtype", [B.BND_F32, B.BND_F64])
+@pytest.mark.parametrize("tune", [dict(seg_len=-1), dict(seg_len=256, warmup=64)])
+def test_padding_never_read_nor_written(dtype, arr, tune):
+    """Pool elements outside every instance (row padding, absent or shorter
+    panel lanes) hold NaN on input and a sentinel on output: the results
+    match the oracle and the sentinel survives everywhere outside."""
+    shapes = [(3000, 2), (2999, 2), (17, 2), (1, 2), (700, 5), (650, 5), (9, 3)]
+    insts, lay, plan = setup(shapes, 3, dtype, tune, arr=arr)
+    sentinel = 7.25
+    got = run_gmm(lay, plan, insts, pad=np.nan, out_fill=sentinel)
+    res, _ = O.batch_step(insts)
+    inside_b = np.zeros(lay.band_elems, bool)
+    inside_r = np.zeros(lay.rhs_elems, bool)
+    for i in range(lay.count):
+        lay.band_view(inside_b, i)[: lay.ls[i] + 1] = True
+        lay.rhs_view(inside_r, i)[: lay.k] = True
+    for key, inside in (("L", inside_b), ("S", inside_b), ("Qb", inside_b), ("X", inside_r), ("Bb", inside_r)):
+        a = got[key].cpu().numpy()
+        assert np.all(a[~inside] == sentinel), f"{key}: a write landed outside the instances"
+    tol = TOL[dtype]
+    for key, ref_key, unpack, t in (("L", "L", lay.unpack_band, "fwd"), ("S", "S", lay.unpack_band, "fwd"),
+                                    ("Qb", "Qbar", lay.unpack_band, "grad"), ("X", "X", lay.unpack_rhs, "fwd"),
+                                    ("Bb", "Bbar", lay.unpack_rhs, "grad")):
+        arrs = unpack(got[key])
+        for c, r in enumerate(res):
+            assert np.all(np.isfinite(arrs[c])), key
+            assert_close(key, arrs[c], r[ref_key], tol[t])
