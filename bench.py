@@ -175,7 +175,7 @@ def run_ours(args, rank, world, device_index):
     torch.cuda.set_device(device_index)
     from paper_1902_10078_gb300 import build as bld
     bld.build()
-    tuning = dict(seg_len=args.seg_len, warmup=args.warm)
+    tuning = dict(seg_len=args.seg_len, warmup=args.warm, flags=args.flags)
     plan = BT.Plan(lay, tuning)
     expect = B.LAYOUT_PANELS if panels else B.LAYOUT_ROWS
     assert B.bnd_plan_layout(plan.handle) == expect, "the plan did not take the intended arrangement"
@@ -361,8 +361,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--k", type=int, default=4)
-    ap.add_argument("--seg-len", type=int, default=2048)
+    ap.add_argument("--seg-len", type=int, default=0, help="rows per segment (0: the library default)")
     ap.add_argument("--warm", type=int, default=0, help="warm-up rows (0: per-bandwidth default)")
+    ap.add_argument("--flags", type=int, default=0, help="plan tuning flags (see bnd_tuning)")
     ap.add_argument("--ls", default="1,2,3,5,7", help="bandwidths drawn uniformly (profiling cases)")
     ap.add_argument("--layout", default="panels", choices=["panels", "rows"],
                     help="pool arrangement: 32-instance panels (cs = 32) or one contiguous row per diagonal")
@@ -424,7 +425,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "layout": LAYOUT_NOTE[args.layout],
                    "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
-                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len, "warmup_rows": args.warm or "24 l + 32",
+                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len or ("library default: 384" if args.layout == "panels" else "library default: 2048"), "warmup_rows": args.warm or "24 l + 32",
                    "chains": r["plan"].chains, "warp_tasks": r["plan"].tasks, "graph": True,
                    "l2": "inputs (~%.1f GB) exceed L2; no flush" % (r["h2d"] / 1e9),
                    "parallelism": f"instances sharded per GPU (weak), dp{world}", "segment_fixups": r["fixups"]},

@@ -33,7 +33,8 @@
  *    most 32 consecutive descriptors whose offsets step by one -- the p-th
  *    descriptor of the run ("lane" p) has band = band_g + p and
  *    rhs = rhs_g + p -- and which share l, ld and ldr; ld and ldr are
- *    multiples of 32 and band_g, rhs_g multiples of 16 bytes.  A descriptor
+ *    multiples of 32, (l+1) ld and k ldr below 2^31 elements, and band_g,
+ *    rhs_g multiples of 16 bytes.  A descriptor
  *    that does not continue the previous run starts a new group.  Row d,
  *    column j of the 32 lanes are then 32 adjacent elements, so one warp
  *    moves whole 128-byte (FP32) lines: this is the layout that reaches HBM
@@ -104,11 +105,14 @@ typedef struct {
 /* Scheduling knobs (all optional; zero fields take the library defaults). */
 typedef struct {
     int64_t seg_len;     /* rows per chain segment; long instances are split into segments
-                            run in parallel (0 = default, < 0 = never split) */
+                            run in parallel (0 = default: 2048 for rows, 384 for panels;
+                            < 0 = never split) */
     int32_t warmup;      /* warm-up rows of a speculative segment start (0 = default:
                             24 l + 32 rows in FP32, 48 l + 64 in FP64) */
     int32_t blocks_per_sm; /* persistent-grid occupancy (0 = default) */
-    int32_t flags;       /* bit 0: never use the shared-memory staged kernels */
+    int32_t flags;       /* bit 0: never use the shared-memory staged kernels;
+                            bit 1: segment length seg_len * warmup / 128 (the same share of
+                            warm-up rows for every bandwidth) */
 } bnd_tuning;
 
 typedef struct bnd_plan bnd_plan;

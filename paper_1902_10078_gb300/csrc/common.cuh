@@ -118,6 +118,7 @@ struct bnd_plan {
     int32_t layout;            // kLayoutRows, kLayoutPanels or kLayoutStrided
     int32_t staged_ok;         // every offset / stride allows 16-byte tiles
     int32_t force_direct;      // tuning: never use the staged kernels
+    int32_t seg_by_warm;       // tuning: segment length proportional to the warm-up
     cudaStream_t side[bnd::kRegMaxL + 1];
     cudaEvent_t ev_fork;
     cudaEvent_t ev_join[bnd::kRegMaxL + 1];

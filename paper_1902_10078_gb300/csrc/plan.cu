@@ -14,7 +14,12 @@ using namespace bnd;
 
 namespace {
 
-constexpr int64_t kDefaultSegLen = 2048;
+// Default segment length (rows).  Row plans: long segments, because the
+// per-lane streams make DRAM, not latency, the limit and more chains only add
+// warm-up rows.  Panel plans: short segments, because their sweeps are bound
+// by the latency of the per-row recurrence and need many resident chains.
+constexpr int64_t kDefaultSegLenRows = 2048;
+constexpr int64_t kDefaultSegLenPanels = 384;
 
 // Default warm-up of a speculative segment start.  The cold-started state
 // forgets its start at a rate per block of l rows, so the warm-up grows with
@@ -49,6 +54,8 @@ bool detect_panels(int32_t count, const bnd_inst *inst, int32_t k, int64_t tw, s
     for (int32_t i = 0; i < count; ++i) {
         const bnd_inst &I = inst[i];
         if (I.cs != kPanelLanes || I.ld % kPanelLanes || (k > 0 && I.ldr % kPanelLanes)) return false;
+        // the panel kernels address a group's region with 32-bit element offsets
+        if ((int64_t)(I.l + 1) * I.ld > INT32_MAX || (int64_t)k * I.ldr > INT32_MAX) return false;
         bool cont = false;
         if (!groups.empty()) {
             const int32_t g0 = groups.back();
@@ -107,12 +114,13 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->k = k;
     const size_t esz = dtype == BND_F32 ? 4 : 8;
     p->warm = 0;                                      // 0: per-bandwidth default
-    p->seg_len = kDefaultSegLen;
+    p->seg_len = 0;
     if (tuning) {
         if (tuning->seg_len != 0) p->seg_len = tuning->seg_len;
         if (tuning->warmup > 0) p->warm = tuning->warmup;
         if (tuning->blocks_per_sm > 0) p->blocks_per_sm = tuning->blocks_per_sm;
         p->force_direct = (tuning->flags & 1) != 0;
+        p->seg_by_warm = (tuning->flags & 2) != 0;
     }
     const int64_t tw = 16 / (int64_t)esz;                 // elements per 16-byte tile
     p->staged_ok = 1;
@@ -129,6 +137,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
                 for (int32_t i = groups[g]; i < groups[g + 1]; ++i) group_of[(size_t)i] = (int32_t)g;
     }
     const bool panels = p->layout == kLayoutPanels;
+    if (p->seg_len == 0) p->seg_len = panels ? kDefaultSegLenPanels : kDefaultSegLenRows;
 
     std::vector<InstDev> idev((size_t)count);
     int64_t nsegs = 0;
@@ -143,6 +152,10 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         const bool reg = I.l >= 1 && I.l <= kRegMaxL;
         if (!reg) has_generic = true;
         D.warm = p->warm > 0 ? ((int64_t)p->warm + 3) / 4 * 4 : default_warm(dtype, I.l);
+        // segment length: the same for every bandwidth, or (flag) scaled with the warm-up so
+        // that every bandwidth pays the same fraction of extra rows (seg_len at 128 warm-up rows)
+        int64_t seg_len = p->seg_len;
+        if (seg_len > 0 && p->seg_by_warm) seg_len = std::max<int64_t>(64, seg_len * D.warm / 128);
         int64_t nseg = 1, len = I.n;
         if (panels) {
             // one segment length for the whole group, set by its longest member
@@ -150,10 +163,10 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
             int64_t gn = 0;
             for (int32_t q = g0; q < g1; ++q) gn = std::max(gn, inst[q].n);
             int64_t gseg = 1;
-            segmentation(gn, p->seg_len, D.warm, reg, &gseg, &len);
+            segmentation(gn, seg_len, D.warm, reg, &gseg, &len);
             nseg = (I.n + len - 1) / len;
         } else {
-            segmentation(I.n, p->seg_len, D.warm, reg, &nseg, &len);
+            segmentation(I.n, seg_len, D.warm, reg, &nseg, &len);
             if (I.band % tw || I.ld % tw || (k > 0 && (I.rhs % tw || I.ldr % tw))) p->staged_ok = 0;
         }
         D.nseg = (int32_t)nseg;

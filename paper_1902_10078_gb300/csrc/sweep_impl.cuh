@@ -259,7 +259,7 @@ struct FwdReg {
             Lc[0] = piv * rinv;
             _Pragma("unroll") for (int d = 1; d <= L; ++d) Lc[d] = a[d] * rinv;
             if (out) {
-                _Pragma("unroll") for (int d = 0; d <= L; ++d) io.out(d, j, tp, inb<CHECK>(j + d, n) ? Lc[d] : T(0));
+                _Pragma("unroll") for (int d = 0; d <= L; ++d) io.template out<CHECK>(d, j, tp, inb<CHECK>(j + d, n) ? Lc[d] : T(0));
                 ld.add(piv);
             }
             // pending sums for the window of column j+1: pair (a', b') <- (a'+1, b'+1) + Lc[1+a'] Lc[1+b']
@@ -308,8 +308,8 @@ struct FwdReg {
                 T s = T(0);
                 _Pragma("unroll") for (int t = 1; t <= L; ++t) s = fma(bU[t], Lc[t], s);
                 T r2 = rinv * rinv;
-                io.out(0, j, tp, T(-2) * bvi2 * r2 * rinv - s * r2);
-                _Pragma("unroll") for (int t = 1; t <= L; ++t) io.out(t, j, tp, inb<CHECK>(i + t, n) ? bU[t] * rinv : T(0));
+                io.template out<CHECK>(0, j, tp, T(-2) * bvi2 * r2 * rinv - s * r2);
+                _Pragma("unroll") for (int t = 1; t <= L; ++t) io.template out<CHECK>(t, j, tp, inb<CHECK>(i + t, n) ? bU[t] * rinv : T(0));
             }
             // the next row comes from the block; then shift the block to rows/cols i+2..i+L+1
             _Pragma("unroll") for (int d = 0; d < L; ++d) srow[d] = sblk[tri(0, d, L)];
@@ -326,7 +326,7 @@ struct FwdReg {
             _Pragma("unroll") for (int r = 0; r < KK; ++r) {
                 const bool on = r < A.kk;
                 T y = ((on ? io.in(I_RHS + r, j, tp) : T(0)) - u[r][0]) * rinv;
-                if (out) io.out(O_RHS + r, j, tp, y);
+                if (out) io.template out<CHECK>(O_RHS + r, j, tp, y);
                 _Pragma("unroll") for (int d = 0; d < L; ++d) {
                     T old = (d + 1 < L) ? u[r][d + 1] : T(0);
                     u[r][d] = fma(Lc[1 + d], y, old);
@@ -458,7 +458,7 @@ struct BwdReg {
                 _Pragma("unroll") for (int t = L; t >= 1; --t) s = fma(U[t], row[t], s);
                 row[0] = rinv * rinv - s;
             }
-            if (out) { _Pragma("unroll") for (int q = 0; q <= L; ++q) io.out(q, j, tp, inb<CHECK>(i + q, n) ? row[q] : T(0)); }
+            if (out) { _Pragma("unroll") for (int q = 0; q <= L; ++q) io.template out<CHECK>(q, j, tp, inb<CHECK>(i + q, n) ? row[q] : T(0)); }
             // shift: new block rows/cols i..i+L-1 : (0, q) <- row[q]; (t, q) <- old (t-1, q-1)
             T nblk[NT];
             _Pragma("unroll") for (int q = 0; q < L; ++q) nblk[tri(0, q, L)] = inb<CHECK>(i + q, n) ? row[q] : T(0);
@@ -498,7 +498,7 @@ struct BwdReg {
                 Lb[0] = fma(-Qb[d], Lc[d], Lb[0]);
             }
             Qb[0] = T(0.5) * Lb[0] * rinv;
-            if (out) { _Pragma("unroll") for (int d = 0; d <= L; ++d) io.out(d, j, tp, inb<CHECK>(j + d, n) ? Qb[d] : T(0)); }
+            if (out) { _Pragma("unroll") for (int d = 0; d <= L; ++d) io.template out<CHECK>(d, j, tp, inb<CHECK>(j + d, n) ? Qb[d] : T(0)); }
             // new pending for iteration j-1 (entries (j+f', j-1-e')): carry old (e, f), e >= 1 -> (e-1, f+1)
             T np[NT];
             _Pragma("unroll") for (int e2 = 0; e2 < L; ++e2)
@@ -533,7 +533,7 @@ struct BwdReg {
             _Pragma("unroll") for (int x = 0; x < NT; ++x) lwin[x] = nw[x];
         }
         if (SOLVE) {
-            if (out) { _Pragma("unroll") for (int r = 0; r < KK; ++r) io.out(O_RHS + r, j, tp, xj[r]); }
+            if (out) { _Pragma("unroll") for (int r = 0; r < KK; ++r) io.template out<CHECK>(O_RHS + r, j, tp, xj[r]); }
             _Pragma("unroll") for (int r = 0; r < KK; ++r) {
                 _Pragma("unroll") for (int d = L - 1; d >= 1; --d) xw[r][d] = xw[r][d - 1];
                 xw[r][0] = xj[r];

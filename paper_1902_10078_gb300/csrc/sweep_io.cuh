@@ -110,6 +110,7 @@ struct DirectIO {
         if (c < 0 || c >= P.n || !P.active(s)) return T(0);
         return P.in_row(s)[c * P.cs];
     }
+    template <bool CHECK>
     __device__ __forceinline__ void out(int O, int64_t j, int, T v) {
         const StreamSpec s = SW::out_spec(O);
         if (!P.active(s)) return;
@@ -238,6 +239,7 @@ struct StagedIO {
         return curR[base(S) + u];
     }
 
+    template <bool CHECK>
     __device__ __forceinline__ void out(int O, int64_t, int u, T v) { outb[O * kWarp * TW + u] = v; }
 
     // Write the out tile of tile m (columns [m TW, m TW + TW) intersected with [a, b) and [0, n)):
@@ -296,66 +298,104 @@ struct PanelIO {
     static constexpr bool kWarpUniform = true;
     static_assert(kPieces >= 1, "a tile must give every lane at least one 16-byte piece");
 
-    const ChainPtrs<T> &P;          // this lane's pools (outputs)
-    const SweepArgs<T> &A;          // pool bases (inputs, addressed by the group)
-    const Task &G;                  // group geometry
+    // column offsets of the input streams (a tile of every stream is inside
+    // [0, gn) when m TW + kMinOff >= 0 and m TW + TW + kMaxOff <= gn)
+    __host__ __device__ static constexpr int min_off() {
+        int v = 0;
+        for (int S = 0; S < NIN; ++S) v = SW::in_spec(S).off < v ? SW::in_spec(S).off : v;
+        return v;
+    }
+    __host__ __device__ static constexpr int max_off() {
+        int v = 0;
+        for (int S = 0; S < NIN; ++S) v = SW::in_spec(S).off > v ? SW::in_spec(S).off : v;
+        return v;
+    }
+
+    // Offsets inside a group's region fit in 32 bits (the plan checks
+    // (l + 1) ld and k ldr against 2^31), so every address below is a 64-bit
+    // pool base plus a 32-bit element offset.
+    const T *gin[7];                // per input pool: base of lane 0's row 0 (RHS: of column rhs0)
+    T *gout[5];                     // per output pool: base of this lane's row 0 (RHS: column rhs0)
+    int32_t gld, gldr;              // row strides of the group (elements)
+    int64_t gn;                     // rows present in the group
+    int32_t kk;                     // active RHS columns of the launch
+    int32_t acc;
+    int64_t n;                      // this lane's order (corner test of the checked stores)
     T *ring;                        // the warp's ring
     int lane;
     int cR, iR;                     // ring slots of the current row tile and of the next one to issue
     const T *cur;                   // this lane's column in the current slot
 
-    __device__ PanelIO(const ChainPtrs<T> &p, const SweepArgs<T> &a, const Task &g, T *warp_smem, int lane_)
-        : P(p), A(a), G(g), ring(warp_smem), lane(lane_) {}
+    __device__ PanelIO(const ChainPtrs<T> &p, const SweepArgs<T> &A, const Task &g, T *warp_smem, int lane_)
+        : ring(warp_smem), lane(lane_) {
+        gld = (int32_t)g.gld;
+        gldr = (int32_t)g.gldr;
+        gn = g.gn;
+        kk = p.kk;
+        acc = p.acc;
+        n = p.n;
+        const int64_t r0 = (int64_t)p.rhs0 * g.gldr;
+        gin[POOL_Q] = A.Q + g.gband;
+        gin[POOL_LIN] = A.Lin + g.gband;
+        gin[POOL_S] = A.S + g.gband;
+        gin[POOL_SBAR] = A.Sbar + g.gband;
+        gin[POOL_LBARIN] = A.Lbar_in + g.gband;
+        gin[POOL_BIN] = A.Bin + g.grhs + r0;
+        gin[POOL_XIN] = A.Xin + g.grhs + r0;
+        gout[POOL_LOUT - POOL_LOUT] = A.L + g.gband + lane;
+        gout[POOL_LBAR - POOL_LOUT] = A.Lbar + g.gband + lane;
+        gout[POOL_SOUT - POOL_LOUT] = A.Sout + g.gband + lane;
+        gout[POOL_QBAR - POOL_LOUT] = A.Qbar + g.gband + lane;
+        gout[POOL_XOUT - POOL_LOUT] = A.Xout + g.grhs + r0 + lane;
+    }
 
     __device__ static __forceinline__ int wrap_add(int x, int d) {
         x += d;
         return x >= R ? x - R : (x < 0 ? x + R : x);
     }
-
-    // Row `s.row` of the stream's pool for lane 0 of the group.
-    __device__ __forceinline__ const T *group_row(const StreamSpec &s) const {
-        const T *base = nullptr;
-        switch (s.pool) {
-            case POOL_Q: base = A.Q; break;
-            case POOL_LIN: base = A.Lin; break;
-            case POOL_S: base = A.S; break;
-            case POOL_SBAR: base = A.Sbar; break;
-            case POOL_LBARIN: base = A.Lbar_in; break;
-            case POOL_BIN: base = A.Bin; break;
-            default: base = A.Xin; break;
-        }
-        if (is_rhs_pool(s.pool)) return base + G.grhs + (int64_t)(P.rhs0 + s.row) * G.gldr;
-        return base + G.gband + (int64_t)s.row * G.gld;
+    __device__ __forceinline__ int32_t row_off(const StreamSpec &s) const {
+        return s.row * (is_rhs_pool(s.pool) ? gldr : gld);
     }
+    __device__ __forceinline__ bool active(const StreamSpec &s) const { return !is_rhs_pool(s.pool) || s.row < kk; }
 
     // Copy into slot q the block of stream S for row tile m: columns
     // m TW + off .. + TW - 1 of all 32 lanes.  Columns outside [0, gn) are
-    // zero filled, not read.
+    // zero filled, not read (ALL: the caller knows every column is inside).
+    template <bool ALL>
     __device__ __forceinline__ void issue(int S, int64_t m, int q) {
         const StreamSpec s = SW::in_spec(S);
         const int64_t c0 = m * TW + s.off;
-        const bool act = P.active(s);
-        const T *row = group_row(s);
+        const bool act = active(s);
+        const T *base = gin[s.pool];
         T *dst = ring + (S * R + q) * kTileElems;
 #pragma unroll
         for (int t = 0; t < kPieces; ++t) {
             const int e = (lane + kWarp * t) * kPieceElems;        // element offset inside the block
-            const int64_t c = c0 + e / kWarp;
-            const bool valid = act && c >= 0 && c < G.gn;
+            bool valid = act;
+            if (!ALL) {
+                const int64_t c = c0 + e / kWarp;
+                valid = valid && c >= 0 && c < gn;
+            }
             // an invalid piece reads nothing (source size 0): the address is only a placeholder
-            cp_async16(dst + e, valid ? row + c0 * kWarp + e : row, valid);
+            const int32_t o = valid ? row_off(s) + (int32_t)c0 * kWarp + e : 0;
+            cp_async16(dst + e, base + o, valid);
         }
     }
+    template <bool ALL>
     __device__ __forceinline__ void issue_all(int64_t m, int q) {
 #pragma unroll
-        for (int S = 0; S < NIN; ++S) issue(S, m, q);
+        for (int S = 0; S < NIN; ++S) issue<ALL>(S, m, q);
+    }
+    __device__ __forceinline__ void issue_tile(int64_t m, int q) {
+        if (m * TW + min_off() >= 0 && m * TW + TW + max_off() <= gn) issue_all<true>(m, q);
+        else issue_all<false>(m, q);
     }
 
     __device__ void begin_tiles(int64_t m0, int64_t, int64_t) {
         cR = (int)(((m0 % R) + R) % R);
         iR = cR;
         for (int t = 0; t < R - 1; ++t) {
-            issue_all(m0 + DIR * t, iR);
+            issue_tile(m0 + DIR * t, iR);
             cp_async_commit();
             iR = wrap_add(iR, DIR);
         }
@@ -363,7 +403,7 @@ struct PanelIO {
 
     __device__ __forceinline__ void tile_begin(int64_t m) {
         __syncwarp();                      // every lane is done with the slot about to be refilled
-        issue_all(m + DIR * (R - 1), iR);
+        issue_tile(m + DIR * (R - 1), iR);
         cp_async_commit();
         iR = wrap_add(iR, DIR);
         cp_async_wait<R - 1>();
@@ -374,12 +414,23 @@ struct PanelIO {
 
     __device__ __forceinline__ T in(int S, int64_t, int u) const { return cur[S * R * kTileElems + u * kWarp]; }
 
+    // Every lane stores its own element; the warp's stores of one column are
+    // one contiguous run of 32 elements.  Interior tiles (CHECK false) of a
+    // launch that does not accumulate store plainly: the sweep guarantees the
+    // element is inside the matrix there.  (Staging the tile in shared memory
+    // for 16-byte block stores measured slower: the extra shared memory cost
+    // more resident warps than the wider stores gained.)
+    template <bool CHECK>
     __device__ __forceinline__ void out(int O, int64_t j, int, T v) {
         const StreamSpec s = SW::out_spec(O);
-        if (!P.active(s)) return;
-        T *p = P.out_row(s) + j * P.cs;
-        const bool corner = !is_rhs_pool(s.pool) && (j + s.row >= P.n);
-        *p = corner ? T(0) : (P.acc ? (*p + v) : v);
+        if (!active(s)) return;
+        T *p = gout[s.pool - POOL_LOUT] + (row_off(s) + (int32_t)j * kWarp);
+        if (!CHECK && !acc) {
+            *p = v;
+            return;
+        }
+        const bool corner = !is_rhs_pool(s.pool) && (j + s.row >= n);
+        *p = corner ? T(0) : (acc ? (*p + v) : v);
     }
 
     __device__ __forceinline__ void tile_end(int64_t, bool) {}
