@@ -68,18 +68,53 @@ def chain_loss(Q, b, W, grad: bool = True):
 # The precision of the stacked states x_0..x_{n-1} is M^T M with M block
 # lower-bidiagonal: M_00 = C_0^{-1}, M_kk = C_k^{-1}, M_{k,k-1} = -C_k^{-1} A_k,
 # where C_0 = chol(Pinf) and C_k = chol(Sigma(t_k - t_{k-1})).
+#
+# Sigma(D) written out with x = lambda D, q = exp(-2x):
+#   Sigma_00 = s2 (1 - q (1 + 2x + 2x^2))
+#   Sigma_01 = 2 s2 lambda x^2 q
+#   Sigma_11 = s2 lambda^2 (1 - q (1 - 2x + 2x^2))
+# For small x, 1 - q (1 + 2x + 2x^2) = 4/3 x^3 + O(x^4) cancels catastrophically
+# when formed as a difference (the gaps of the workload reach x ~ 1e-5), so
+# both brackets are summed from their Taylor series below x = 1/2.
 # ---------------------------------------------------------------------------
+
+_SERIES_X = 0.5
+_SERIES_TERMS = 40
+
+
+def one_minus_exp_poly(x, c1):
+    """1 - exp(-2x) (1 + c1 x + 2 x^2), elementwise, for c1 = +2 or -2."""
+    x = np.asarray(x, dtype=np.float64)
+    direct = 1.0 - np.exp(-2.0 * x) * (1.0 + c1 * x + 2.0 * x * x)
+    xs = np.minimum(x, _SERIES_X)
+    # coefficient of x^k in exp(-2x) (1 + c1 x + 2 x^2):
+    #   (-2)^k / k! + c1 (-2)^(k-1) / (k-1)! + 2 (-2)^(k-2) / (k-2)!
+    ser = np.zeros_like(xs)
+    xk = np.ones_like(xs)
+    for k in range(1, _SERIES_TERMS + 1):
+        xk = xk * xs
+        a = (-2.0) ** k / math.factorial(k) + c1 * (-2.0) ** (k - 1) / math.factorial(k - 1)
+        if k >= 2:
+            a += 2.0 * (-2.0) ** (k - 2) / math.factorial(k - 2)
+        ser = ser - a * xk
+    return np.where(x < _SERIES_X, ser, direct)
+
 
 def matern_transition(D, ell, s2):
     lam = math.sqrt(3.0) / ell
-    e = np.exp(-lam * D)
+    D = np.asarray(D, dtype=np.float64)
+    x = lam * D
+    e = np.exp(-x)
     A = np.empty(D.shape + (2, 2))
-    A[..., 0, 0] = e * (1.0 + lam * D)
+    A[..., 0, 0] = e * (1.0 + x)
     A[..., 0, 1] = e * D
-    A[..., 1, 0] = -e * lam * lam * D
-    A[..., 1, 1] = e * (1.0 - lam * D)
+    A[..., 1, 0] = -e * lam * x
+    A[..., 1, 1] = e * (1.0 - x)
     Pinf = np.array([[s2, 0.0], [0.0, lam * lam * s2]])
-    Sig = Pinf - A @ Pinf @ np.swapaxes(A, -1, -2)
+    Sig = np.empty(D.shape + (2, 2))
+    Sig[..., 0, 0] = s2 * one_minus_exp_poly(x, 2.0)
+    Sig[..., 0, 1] = Sig[..., 1, 0] = 2.0 * s2 * lam * x * x * np.exp(-2.0 * x)
+    Sig[..., 1, 1] = s2 * lam * lam * one_minus_exp_poly(x, -2.0)
     return A, Sig, Pinf
 
 

@@ -483,3 +483,30 @@ def test_matern_kl_matches_dense_gaussian_kl(oracle):
     ref = 0.5 * (np.trace(Qp @ Sq) + m @ Qp @ m - N + np.linalg.slogdet(np.linalg.inv(Qp))[1]
                  - np.linalg.slogdet(Sq)[1])
     assert abs(kl - ref) < 1e-9 * max(1.0, abs(ref))
+
+
+def test_matern_sigma_matches_definition_and_high_precision(oracle):
+    """Sigma(D) = Pinf - A Pinf A^T: the closed form agrees with the matrix
+    definition where the difference is well conditioned, and with a 50-digit
+    evaluation of the definition at tiny gaps, where the plain difference
+    cancels (relative error of the closed form <= 1e-13 everywhere)."""
+    import mpmath
+    from oracle.losses import matern_transition
+    ell, s2 = 0.7, 1.3
+    lam = math.sqrt(3.0) / ell
+    D = np.array([1e-7, 3e-6, 1e-4, 2e-3, 0.05, 0.2, 0.28, 0.3, 0.5, 1.0, 4.0, 20.0])
+    A, Sig, Pinf = matern_transition(D, ell, s2)
+    plain = Pinf - A @ Pinf @ np.swapaxes(A, -1, -2)
+    big = D * lam > 0.6
+    assert np.max(np.abs(Sig[big] - plain[big]) / np.abs(plain[big]).max(axis=(1, 2), keepdims=True)) < 1e-13
+    mpmath.mp.dps = 50
+    for i, d in enumerate(D):
+        L, dd = mpmath.mpf(lam), mpmath.mpf(float(d))
+        e = mpmath.exp(-L * dd)
+        Am = mpmath.matrix([[e * (1 + L * dd), e * dd], [-e * L * L * dd, e * (1 - L * dd)]])
+        Pm = mpmath.matrix([[s2, 0], [0, L * L * s2]])
+        Sm = Pm - Am * Pm * Am.T
+        for a in range(2):
+            for b in range(2):
+                ref = float(Sm[a, b])
+                assert abs(Sig[i, a, b] - ref) <= 1e-13 * abs(ref), (d, a, b, Sig[i, a, b], ref)
