@@ -167,17 +167,20 @@ def matern_precision(t, ell, s2):
 
 
 def matern_kl(t, ell, s2, Lq, m):
-    """KL(N(m, (Lq Lq^T)^{-1}) || N(0, Q_p^{-1})), Eq. 5 / Alg. 7 with m_p = 0."""
-    Qp = matern_precision(t, ell, s2)
-    Lp, info = cholesky(Qp)
-    if info:
-        raise ValueError(f"prior precision not SPD (info={info})")
+    """KL(N(m, (Lq Lq^T)^{-1}) || N(0, Q_p^{-1})), Eq. 5 / Alg. 7 with m_p = 0.
+
+    The prior precision comes factored, Q_p = M^T M with M lower triangular, so
+    the two terms of Alg. 7 that use a factor of Q_p take M:
+    ||L_p^T (m_p - m_q)||^2 = m^T Q_p m = ||M m||^2 and log det Q_p =
+    2 sum log |M_ii|.  (A Cholesky factor of Q_p itself loses all accuracy at
+    the workload's smallest gaps, where Q_p reaches 1e15 and more.)"""
+    from . import band_matvec
+    M = matern_M_band(t, ell, s2)
+    Qp = product(M, 3, 0, 1, M, 3, 0, 0, 3, 0)
     Sq = subset_inverse(Lq)
     N = Lq.shape[1]
     tr = trace_sym(Sq, Qp)
-    # ||P(Lp^T, m_p - m_q)||^2 with m_p = 0
-    from . import band_matvec
-    v = band_matvec(Lp, 3, 0, 1, -np.asarray(m, dtype=np.float64))
+    v = band_matvec(M, 3, 0, 0, np.asarray(m, dtype=np.float64)[None])[0]
     quad = float(v @ v)
-    logs = 2.0 * float(np.sum(np.log(Lq[0]) - np.log(Lp[0])))
+    logs = 2.0 * float(np.sum(np.log(Lq[0]))) - 2.0 * float(np.sum(np.log(np.abs(M[0]))))
     return 0.5 * (tr + logs + quad - N)

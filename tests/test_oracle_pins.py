@@ -510,3 +510,46 @@ def test_matern_sigma_matches_definition_and_high_precision(oracle):
             for b in range(2):
                 ref = float(Sm[a, b])
                 assert abs(Sig[i, a, b] - ref) <= 1e-13 * abs(ref), (d, a, b, Sig[i, a, b], ref)
+
+
+def test_matern_kl_at_tiny_gaps_matches_high_precision(oracle):
+    """With a gap of 1e-6 the prior precision reaches ~1e17: the oracle KL
+    (closed-form Sigma, factor M for the quadratic term and the log-det) still
+    matches a 60-digit dense evaluation of the Gaussian KL."""
+    import mpmath
+    from oracle.losses import matern_kl
+    mpmath.mp.dps = 60
+    rng = W.rng_for(97)
+    n = 6
+    gaps = np.array([0.7, 1e-6, 1.3, 0.2, 2e-4])
+    t = np.concatenate([[0.0], np.cumsum(gaps)])
+    ell, s2 = 1.1, 1.0
+    N = 2 * n
+    Lq = np.zeros((4, N))
+    Lq[0] = 1.0 + 0.1 * rng.uniform(size=N)
+    Lq[1:] = rng.normal(0.0, 0.05, (3, N))
+    W.zero_corners(Lq)
+    m = rng.normal(0.0, 0.1, N)
+    kl = matern_kl(t, ell, s2, Lq, m)
+    lam = mpmath.sqrt(3) / ell
+    K = mpmath.matrix(N, N)
+    for a in range(n):
+        for b in range(n):
+            tau = mpmath.mpf(float(t[a])) - mpmath.mpf(float(t[b]))
+            e = mpmath.exp(-lam * abs(tau))
+            K[2 * a, 2 * b] = s2 * (1 + lam * abs(tau)) * e
+            K[2 * a, 2 * b + 1] = s2 * lam * lam * tau * e
+            K[2 * a + 1, 2 * b] = -s2 * lam * lam * tau * e
+            K[2 * a + 1, 2 * b + 1] = s2 * lam * lam * (1 - lam * abs(tau)) * e
+    Qp = mpmath.inverse(K)
+    Ld = mpmath.matrix(N, N)
+    for d in range(4):
+        for j in range(N - d):
+            Ld[j + d, j] = mpmath.mpf(float(Lq[d, j]))
+    Qq = Ld * Ld.T
+    Sq = mpmath.inverse(Qq)
+    mv = mpmath.matrix([mpmath.mpf(float(x)) for x in m])
+    tr = sum(Qp[i, j] * Sq[j, i] for i in range(N) for j in range(N))
+    quad = (mv.T * Qp * mv)[0]
+    ref = 0.5 * (tr + quad - N + mpmath.log(mpmath.det(Qq)) - mpmath.log(mpmath.det(Qp)))
+    assert abs(kl - float(ref)) <= 1e-9 * abs(float(ref)), (kl, float(ref))
