@@ -5,6 +5,9 @@ backward calls the hand-written adjoint kernel (Alg. 2 for the Cholesky,
 Alg. 4 for the subset inverse, the Table 1 compositions for solves and
 products).  Tensors are the flat band / RHS pools of a ``batch.Layout``; the
 ``Plan`` fixes the batch.  Torch allocates outputs and zero cotangents only.
+Outputs are zero-initialised: the kernels write only the entries of the
+instances, so pool elements outside them (row padding, absent panel lanes)
+read as 0 in reductions over whole pools.
 """
 from __future__ import annotations
 
@@ -23,7 +26,7 @@ class Cholesky(torch.autograd.Function):
     @staticmethod
     def forward(ctx, plan, Q):
         lay = plan.layout
-        L = torch.empty_like(Q)
+        L = torch.zeros_like(Q)
         logdet = torch.empty(lay.count, dtype=torch.float64, device=Q.device)
         info = torch.empty(lay.count, dtype=torch.int32, device=Q.device)
         B.banded_cholesky(plan.handle, Q.contiguous(), L, logdet, info)
@@ -37,7 +40,7 @@ class Cholesky(torch.autograd.Function):
         (L,) = ctx.saved_tensors
         Lbar = _zeros_like_or(Lbar, L)
         ldbar = None if ldbar is None else ldbar.contiguous().to(torch.float64)
-        Qbar = torch.empty_like(L)
+        Qbar = torch.zeros_like(L)
         B.banded_cholesky_vjp(ctx.plan.handle, L, Lbar, ldbar, Qbar, 0)
         return None, Qbar
 
@@ -47,7 +50,7 @@ class Solve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, plan, L, Bm, mode):
-        X = torch.empty_like(Bm)
+        X = torch.zeros_like(Bm)
         B.banded_solve(plan.handle, L.contiguous(), Bm.contiguous(), X, int(mode))
         ctx.plan, ctx.mode = plan, int(mode)
         ctx.save_for_backward(L, X)
@@ -56,8 +59,8 @@ class Solve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, Xbar):
         L, X = ctx.saved_tensors
-        Bbar = torch.empty_like(X)
-        Lbar = torch.empty_like(L) if ctx.needs_input_grad[1] else None
+        Bbar = torch.zeros_like(X)
+        Lbar = torch.zeros_like(L) if ctx.needs_input_grad[1] else None
         B.banded_solve_vjp(ctx.plan.handle, L, X, Xbar.contiguous(), ctx.mode, Bbar, Lbar, 0)
         return None, Lbar, Bbar, None
 
@@ -67,7 +70,7 @@ class SubsetInverse(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, plan, L):
-        S = torch.empty_like(L)
+        S = torch.zeros_like(L)
         B.banded_subset_inverse(plan.handle, L.contiguous(), S)
         ctx.plan = plan
         ctx.save_for_backward(L, S)
@@ -76,7 +79,7 @@ class SubsetInverse(torch.autograd.Function):
     @staticmethod
     def backward(ctx, Sbar):
         L, S = ctx.saved_tensors
-        Lbar = torch.empty_like(L)
+        Lbar = torch.zeros_like(L)
         B.banded_subset_inverse_vjp(ctx.plan.handle, L, S, Sbar.contiguous(), Lbar, 0)
         return None, Lbar
 
@@ -110,7 +113,7 @@ class Matvec(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, plan, A, a_band, transA, V):
-        P = torch.empty_like(V)
+        P = torch.zeros_like(V)
         B.banded_matvec(plan.handle, A.contiguous(), a_band[0], a_band[1], transA, V.contiguous(), P, 0)
         ctx.plan, ctx.args = plan, (a_band, transA)
         ctx.save_for_backward(A, V)
@@ -130,7 +133,7 @@ class Matvec(torch.autograd.Function):
             else:
                 B.banded_outer(ctx.plan.handle, Pbar, V, Abar, a_band[0], a_band[1], 0)
         if ctx.needs_input_grad[4]:
-            Vbar = torch.empty_like(V)
+            Vbar = torch.zeros_like(V)
             B.banded_matvec(ctx.plan.handle, A, a_band[0], a_band[1], 1 - transA, Pbar, Vbar, 0)
         return None, Abar, None, None, Vbar
 
@@ -142,7 +145,7 @@ class GMMStep(torch.autograd.Function):
     @staticmethod
     def forward(ctx, plan, Q, Bm):
         lay = plan.layout
-        L, S, X = torch.empty_like(Q), torch.empty_like(Q), torch.empty_like(Bm)
+        L, S, X = torch.zeros_like(Q), torch.zeros_like(Q), torch.zeros_like(Bm)
         logdet = torch.empty(lay.count, dtype=torch.float64, device=Q.device)
         info = torch.empty(lay.count, dtype=torch.int32, device=Q.device)
         B.banded_gmm_forward(plan.handle, Q.contiguous(), Bm.contiguous(), L, X, S, logdet, info)
@@ -157,7 +160,7 @@ class GMMStep(torch.autograd.Function):
         Xbar = _zeros_like_or(Xbar, X)
         Sbar = _zeros_like_or(Sbar, S)
         ldbar = None if ldbar is None else ldbar.contiguous().to(torch.float64)
-        Qbar, Bbar = torch.empty_like(L), torch.empty_like(X)
+        Qbar, Bbar = torch.zeros_like(L), torch.zeros_like(X)
         B.banded_gmm_backward(ctx.plan.handle, L, X, S, Xbar, Sbar, ldbar, Qbar, Bbar)
         return None, Qbar, Bbar
 

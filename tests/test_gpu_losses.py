@@ -1,0 +1,169 @@
+"""GPU: the workload losses composed from the CUDA operators, forward and
+reverse mode through the torch.autograd.Function adjoints.
+
+* Long chain (n = 100000, l = 3, one RHS): loss = -1/2 b^T Q^{-1} b +
+  1/2 log det Q + 1/2 tr(band(Q^{-1}) W).  Value and stored-entry gradient
+  against the FP64 oracle composition; in FP64 the autograd gradient also
+  matches central finite differences of the GPU loss on 50 random stored
+  entries.
+* Matern-3/2 state-space KL: sum over processes of KL(N(m, (Lq Lq^T)^{-1}) ||
+  N(0, Q_p^{-1})) with Q_p = M^T M built from (t, lengthscale).  Value against
+  the oracle; gradients in the lengthscales, Lq and m against central finite
+  differences of the oracle's KL.  The full-size batch (256 processes,
+  N = 100000 states each) checks the value.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import losses as OL
+from paper_1902_10078_gb300 import batch as BT
+from paper_1902_10078_gb300 import binding as B
+from paper_1902_10078_gb300 import losses as LS
+from paper_1902_10078_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import paper_1902_10078_gb300.build as bld
+    bld.build()
+    O.lib()
+
+
+def rounded(a, dtype):
+    return np.asarray(a, dtype=BT.NP_DT[dtype]).astype(np.float64)
+
+
+# --------------------------------------------------------------------------- long chain
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_long_chain_loss_and_gradient(dtype):
+    n, l = 100_000, 3
+    Q, b, Wt = W.long_chain_config(n, l)
+    Q, b, Wt = rounded(Q, dtype), rounded(b, dtype), rounded(Wt, dtype)
+    lay = BT.Layout([n], [l], 1, dtype)
+    plan = BT.Plan(lay)
+    Qd = torch.tensor(lay.pack_band([Q]), device="cuda", requires_grad=True)
+    bd = torch.tensor(lay.pack_rhs([b[None]]), device="cuda")
+    Wd = torch.tensor(lay.pack_band([Wt]), device="cuda")
+    wsym = LS.symmetric_weights(lay)
+    loss, info = LS.chain_loss(plan, Qd, bd, Wd, wsym)
+    loss.backward()
+    assert int(info.abs().sum()) == 0
+    ref_loss, ref_Qbar = OL.chain_loss(Q, b, Wt)
+    tol_v, tol_g = (1e-10, 1e-10) if dtype == B.BND_F64 else (1e-4, 1e-3)
+    assert abs(float(loss.detach()) - ref_loss) <= tol_v * max(1.0, abs(ref_loss))
+    g = lay.unpack_band(Qd.grad)[0]
+    err = np.max(np.abs(g - ref_Qbar)) / np.max(np.abs(ref_Qbar))
+    assert err <= tol_g, err
+    if dtype != B.BND_F64:
+        return
+    rng = W.rng_for(4242)
+    view = lay.band_view(Qd.data, 0)
+    with torch.no_grad():
+        for _ in range(50):
+            d, j = int(rng.integers(0, l + 1)), int(rng.integers(0, n - l))
+            h = 1e-5 * max(1.0, abs(Q[d, j]))
+            old = float(view[d, j])
+            view[d, j] = old + h
+            lp = float(LS.chain_loss(plan, Qd, bd, Wd, wsym)[0])
+            view[d, j] = old - h
+            lm = float(LS.chain_loss(plan, Qd, bd, Wd, wsym)[0])
+            view[d, j] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[d, j]) <= 1e-5 * max(1.0, abs(fd)), (d, j, fd, g[d, j])
+
+
+# --------------------------------------------------------------------------- Matern KL
+
+def matern_setup(count, n, dtype, panels=True, seed=W.BASE_SEED, min_gap=0.0):
+    procs = W.matern_batch(count, n, seed)
+    for p in procs:                       # optional floor on the gaps (gradient checks by differences)
+        p.t = p.t + min_gap * np.arange(p.t.shape[0])
+    N = 2 * n
+    lay = BT.Layout([N] * count, [3] * count, 1, dtype, panels=panels)
+    plan = BT.Plan(lay)
+    Lq = torch.tensor(lay.pack_band([rounded(p.Lq, dtype) for p in procs]), device="cuda", requires_grad=True)
+    m = torch.tensor(lay.pack_rhs([rounded(p.m, dtype)[None] for p in procs]), device="cuda", requires_grad=True)
+    ells = torch.tensor([p.lengthscale for p in procs], dtype=torch.float64, device="cuda", requires_grad=True)
+    ctx = dict(index=LS.band_index(lay), ts=[p.t for p in procs], wsym=LS.symmetric_weights(lay),
+               dmask=LS.diagonal_mask(lay))
+    return procs, lay, plan, Lq, m, ells, ctx
+
+
+def gpu_kl(plan, ctx, ells, Lq, m):
+    return LS.matern_kl(plan, ctx["index"], ctx["ts"], ells, 1.0, Lq, m, ctx["wsym"], ctx["dmask"])
+
+
+def oracle_kl(procs, dtype, ells=None, Lqs=None, ms=None):
+    tot = 0.0
+    for i, p in enumerate(procs):
+        ell = p.lengthscale if ells is None else ells[i]
+        Lq = rounded(p.Lq, dtype) if Lqs is None else Lqs[i]
+        m = rounded(p.m, dtype) if ms is None else ms[i]
+        tot += OL.matern_kl(p.t, ell, p.variance, Lq, m)
+    return tot
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_matern_kl_value_and_gradients(dtype):
+    # gaps of at least 0.5 keep Q_p moderate, so that central differences of one
+    # process's KL resolve single-entry gradients (the full-size test keeps the
+    # workload's own gaps)
+    count, n = 6, 1500
+    procs, lay, plan, Lq, m, ells, ctx = matern_setup(count, n, dtype, min_gap=0.5)
+    assert B.bnd_plan_layout(plan.handle) == B.LAYOUT_PANELS
+    kl = gpu_kl(plan, ctx, ells, Lq, m)
+    kl.backward()
+    ref = oracle_kl(procs, dtype)
+    tol_v, tol_g = (1e-10, 1e-6) if dtype == B.BND_F64 else (1e-4, 2e-3)
+    assert abs(float(kl.detach()) - ref) <= tol_v * max(1.0, abs(ref)), (float(kl.detach()), ref)
+    Lqs = [rounded(p.Lq, dtype) for p in procs]
+    ms = [rounded(p.m, dtype) for p in procs]
+
+    def kl_i(i, ell=None, Lq_i=None, m_i=None):
+        p = procs[i]
+        return OL.matern_kl(p.t, p.lengthscale if ell is None else ell, p.variance,
+                            Lqs[i] if Lq_i is None else Lq_i, ms[i] if m_i is None else m_i)
+
+    # lengthscale gradients vs central differences of the oracle KL of that process
+    for i in range(count):
+        e0 = procs[i].lengthscale
+        h = 1e-5 * e0
+        fd = (kl_i(i, ell=e0 + h) - kl_i(i, ell=e0 - h)) / (2 * h)
+        g = float(ells.grad[i])
+        assert abs(g - fd) <= tol_g * max(1.0, abs(fd)), (i, g, fd)
+    # Lq and m gradients on a few entries
+    rng = W.rng_for(77)
+    gL = lay.unpack_band(Lq.grad)
+    gm = lay.unpack_rhs(m.grad)
+    h = 1e-5
+    for _ in range(8):
+        i = int(rng.integers(0, count))
+        d, j = int(rng.integers(0, 4)), int(rng.integers(0, 2 * n - 3))
+        Lp, Lm = Lqs[i].copy(), Lqs[i].copy()
+        Lp[d, j] += h
+        Lm[d, j] -= h
+        fd = (kl_i(i, Lq_i=Lp) - kl_i(i, Lq_i=Lm)) / (2 * h)
+        assert abs(gL[i][d, j] - fd) <= tol_g * max(1.0, abs(fd)), (i, d, j, gL[i][d, j], fd)
+        j = int(rng.integers(0, 2 * n))
+        mp, mm = ms[i].copy(), ms[i].copy()
+        mp[j] += h
+        mm[j] -= h
+        fd = (kl_i(i, m_i=mp) - kl_i(i, m_i=mm)) / (2 * h)
+        assert abs(gm[i][0, j] - fd) <= tol_g * max(1.0, abs(fd)), (i, j, gm[i][0, j], fd)
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_matern_kl_full_size(dtype):
+    count, n = 256, 50_000
+    procs, lay, plan, Lq, m, ells, ctx = matern_setup(count, n, dtype)
+    kl = gpu_kl(plan, ctx, ells, Lq, m)
+    kl.backward()
+    ref = oracle_kl(procs, dtype)
+    tol = 1e-10 if dtype == B.BND_F64 else 1e-4
+    assert abs(float(kl.detach()) - ref) <= tol * max(1.0, abs(ref)), (float(kl.detach()), ref)
+    assert torch.isfinite(ells.grad).all() and torch.isfinite(Lq.grad).all() and torch.isfinite(m.grad).all()
