@@ -421,6 +421,144 @@ def cpu_baseline(args, sample_count=None):
                       f"OpenMP over instances, {dt:.2f} s"}, dt
 
 
+# --------------------------------------------------------------------------- the other configurations
+
+def run_config(args):
+    """Supplementary measurements of the other workload configurations (one
+    JSON line each; the headline line is the uneven batch).  Every number is
+    timed with CUDA events on the launching stream after warm-up calls."""
+    import torch
+
+    from paper_1902_10078_gb300 import batch as BT
+    from paper_1902_10078_gb300 import binding as B
+    from paper_1902_10078_gb300 import build as bld
+    from paper_1902_10078_gb300 import losses as LS
+    torch.cuda.set_device(0)
+    bld.build()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def gmm_setup(shapes, k, dt, tuning=None, panels=False):
+        insts = [W.make_instance(n, l, k, W.BASE_SEED + i) for i, (n, l) in enumerate(shapes)]
+        lay = BT.Layout([s[0] for s in shapes], [s[1] for s in shapes], k, dt, panels=panels)
+        plan = BT.Plan(lay, tuning)
+        dev = {key: torch.from_numpy(pool).cuda() for key, pool in (
+            ("Q", lay.pack_band([i.Q for i in insts])), ("Sbar", lay.pack_band([i.Sbar for i in insts])),
+            ("B", lay.pack_rhs([i.B for i in insts])), ("Xbar", lay.pack_rhs([i.Xbar for i in insts])))}
+        L, S, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool()
+        X, Bb = lay.rhs_pool(), lay.rhs_pool()
+        ld = torch.empty(lay.count, dtype=torch.float64, device="cuda")
+        info = torch.empty(lay.count, dtype=torch.int32, device="cuda")
+        ldb = torch.full((lay.count,), 0.5, dtype=torch.float64, device="cuda")
+
+        def step():
+            B.banded_gmm_forward(plan.handle, dev["Q"], dev["B"], L, X, S, ld, info)
+            B.banded_gmm_backward(plan.handle, L, X, S, dev["Xbar"], dev["Sbar"], ldb, Qb, Bb)
+        return lay, plan, step, info
+
+    lines = []
+    dts = {"f64": B.BND_F64, "f32": B.BND_F32}
+    if args.config == 0:
+        lay, plan, step, info = gmm_setup([(1000, 2)], 1, B.BND_F64, dict(seg_len=-1))
+        ms = timed(step, 200)
+        lines.append({"config": "plain single instance n=1000, l=2, 1 RHS, FP64: fused Cholesky + solve + "
+                      "log-det + subset inverse, forward and backward", "us_per_step": 1e3 * ms,
+                      "bound": "launch latency and the sequential chain (one lane)"})
+    elif args.config == 1:
+        n, l = 100_000, 3
+        Q, b, Wt = W.long_chain_config(n, l)
+        for name, dt in dts.items():
+            lay = BT.Layout([n], [l], 1, dt)
+            plan = BT.Plan(lay)
+            Qd = torch.tensor(lay.pack_band([Q]), device="cuda", requires_grad=True)
+            bd = torch.tensor(lay.pack_rhs([b[None]]), device="cuda")
+            Wd = torch.tensor(lay.pack_band([Wt]), device="cuda")
+            wsym = LS.symmetric_weights(lay)
+
+            def step():
+                Qd.grad = None
+                loss, _ = LS.chain_loss(plan, Qd, bd, Wd, wsym)
+                loss.backward()
+            ms = timed(step, 20)
+            lines.append({"config": f"long chain n={n}, l={l}, loss forward + backward through autograd, {name}",
+                          "ms_per_step": ms, "ns_per_row": 1e6 * ms / n, "segments": plan.chains})
+    elif args.config == 3:
+        # the fused step carries at most 4 RHS; 16 RHS run through the separate operators:
+        # forward C, S (Q^{-1} B, chunks of 4 columns), I; backward solve, subset-inverse and
+        # Cholesky adjoints (accumulating into one L-bar)
+        for l in args.wide_ls:
+            n, k = 200_000, 16
+            ins = W.make_instance(n, l, k, W.BASE_SEED)
+            lay = BT.Layout([n], [l], k, B.BND_F64)
+            plan = BT.Plan(lay, dict(seg_len=-1))
+            Q = torch.from_numpy(lay.pack_band([ins.Q])).cuda()
+            Bm = torch.from_numpy(lay.pack_rhs([ins.B])).cuda()
+            Xb = torch.from_numpy(lay.pack_rhs([ins.Xbar])).cuda()
+            Sb = torch.from_numpy(lay.pack_band([ins.Sbar])).cuda()
+            L, S, Lb, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool(), lay.band_pool()
+            X, Bb = lay.rhs_pool(), lay.rhs_pool()
+            ld = torch.empty(1, dtype=torch.float64, device="cuda")
+            info = torch.empty(1, dtype=torch.int32, device="cuda")
+            ldb = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+
+            def step():
+                B.banded_cholesky(plan.handle, Q, L, ld, info)
+                B.banded_solve(plan.handle, L, Bm, X, 2)
+                B.banded_subset_inverse(plan.handle, L, S)
+                B.banded_solve_vjp(plan.handle, L, X, Xb, 2, Bb, Lb, 0)
+                B.banded_subset_inverse_vjp(plan.handle, L, S, Sb, Lb, 1)
+                B.banded_cholesky_vjp(plan.handle, L, Lb, ldb, Qb, 0)
+            step()                                  # one warm-up call: this path runs for seconds
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            flops = 9.0 * n * l * l
+            lines.append({"config": f"wide band n={n}, l={l}, k={k}, FP64: Cholesky, Q^-1 B, subset inverse "
+                          "and their adjoints", "ms_per_step": ms, "gflops_per_s": flops / (ms * 1e-3) / 1e9,
+                          "info": int(info.item()),
+                          "path": "generic kernels: one lane per instance, windows in memory"})
+    elif args.config == 4:
+        count, n = 256, 50_000
+        procs = W.matern_batch(count, n)
+        for name, dt in dts.items():
+            lay = BT.Layout([2 * n] * count, [3] * count, 1, dt, panels=True)
+            plan = BT.Plan(lay)
+            Lq = torch.tensor(lay.pack_band([p.Lq for p in procs]), device="cuda", requires_grad=True)
+            m = torch.tensor(lay.pack_rhs([p.m[None] for p in procs]), device="cuda", requires_grad=True)
+            ells = torch.tensor([p.lengthscale for p in procs], dtype=torch.float64, device="cuda",
+                                requires_grad=True)
+            prior = LS.MaternPrior(lay, [p.t for p in procs], 1.0)
+            wsym, dmask = LS.symmetric_weights(lay), LS.diagonal_mask(lay)
+
+            def step():
+                Lq.grad = m.grad = ells.grad = None
+                kl = LS.matern_kl(plan, prior, ells, Lq, m, wsym, dmask)
+                kl.backward()
+            ms = timed(step, 5)
+            lines.append({"config": f"Matern-3/2 KL, {count} processes x {2 * n} states, l=3, forward + backward "
+                          f"in L_q, m and the lengthscales, {name}", "ms_per_step": ms,
+                          "band_entries_per_s": count * 2 * n * 4 / (ms * 1e-3),
+                          "note": "includes the FP64 torch construction of the prior factor M (flat over all "
+                                  "processes) and its backward"})
+    for line in lines:
+        print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- main
 
 def main():
@@ -442,6 +580,9 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", type=int, default=None, choices=[0, 1, 3, 4],
+                    help="time another workload configuration instead of the uneven batch")
+    ap.add_argument("--wide-ls", type=int, nargs="+", default=[64], help="bandwidths of --config 3")
     ap.add_argument("--profile-once", action="store_true",
                     help="run one forward and one backward call in NVTX ranges (for ncu) and exit")
     ap.add_argument("--summarize-ncu", default=None, help="ncu --csv file of one backward call -> profiles/")
@@ -450,6 +591,9 @@ def main():
     args = ap.parse_args()
     if args.summarize_ncu:
         summarize_ncu(args)
+        return
+    if args.config is not None:
+        run_config(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import math
 
+import numpy as np
 import torch
 
 from . import autograd as AG
@@ -46,12 +47,6 @@ def diagonal_mask(layout, device="cuda"):
     for i in range(layout.count):
         layout.band_view(w, i)[0, :] = True
     return w.to(device=device)
-
-
-def band_index(layout, device="cuda"):
-    """Flat pool index of every stored entry: per instance an (rows, n) int64 view."""
-    idx = torch.arange(layout.band_elems, dtype=torch.int64)
-    return [layout.band_view(idx, i) for i in range(layout.count)]
 
 
 # ---------------------------------------------------------------------------
@@ -98,71 +93,90 @@ def _bracket(x, coeffs, c1):
     return torch.where(x < _SERIES_X, acc, direct)
 
 
-def matern_M_blocks(t, ell, s2):
-    """Blocks of M for one process: diagonal C_k^{-1} (k = 0..n-1) and
-    sub-diagonal -C_k^{-1} A_k (k = 1..n-1), as (n, 2, 2) and (n-1, 2, 2)
-    FP64 tensors differentiable in ell (a 0-d tensor)."""
-    lam = math.sqrt(3.0) / ell
-    D = t[1:] - t[:-1]
-    x = lam * D
-    e = torch.exp(-x)
-    q = torch.exp(-2.0 * x)
-    s00 = s2 * _bracket(x, _B_PLUS, 2.0)
-    s01 = 2.0 * s2 * lam * x * x * q
-    s11 = s2 * lam * lam * _bracket(x, _B_MINUS, -2.0)
-    # lower Cholesky factors: C_0 of Pinf, C_k of Sigma(D_k)
-    c00 = torch.cat([torch.sqrt(s2 * torch.ones_like(lam)).reshape(1), torch.sqrt(s00)])
-    c10 = torch.cat([torch.zeros(1, dtype=t.dtype, device=t.device), s01 / torch.sqrt(s00)])
-    c11 = torch.cat([(lam * math.sqrt(s2)).reshape(1), torch.sqrt(s11 - (s01 * s01) / s00)])
-    # inverses of the lower 2x2 factors
-    i00, i11 = 1.0 / c00, 1.0 / c11
-    i10 = -c10 / (c00 * c11)
-    # -C_k^{-1} A_k for k >= 1, A_k = e [[1 + x, D], [-lam x, 1 - x]]
-    a00, a01, a10, a11 = e * (1.0 + x), e * D, -e * lam * x, e * (1.0 - x)
-    j00, j10, j11 = i00[1:], i10[1:], i11[1:]
-    o00 = -(j00 * a00)
-    o01 = -(j00 * a01)
-    o10 = -(j10 * a00 + j11 * a10)
-    o11 = -(j10 * a01 + j11 * a11)
-    return (i00, i10, i11), (o00, o01, o10, o11)
+class MaternPrior:
+    """Prior factor M of a batch of Matern-3/2 processes (instance i of the
+    layout is process i, N_i = 2 n_i states), built for all processes at once
+    on flat tensors: the inputs of every process concatenated, gaps and
+    blocks computed elementwise, one scatter into the band pool.  Inputs and
+    pool indices are uploaded once; `band(ells)` is differentiable in the
+    (count,) FP64 lengthscales."""
+
+    def __init__(self, layout, ts, s2, device="cuda"):
+        self.layout, self.s2, self.device = layout, float(s2), device
+        ns = [len(t) for t in ts]
+        self.t = torch.as_tensor(np.concatenate([np.asarray(t, dtype=np.float64) for t in ts]), device=device)
+        self.proc = torch.repeat_interleave(torch.arange(len(ts), device=device),
+                                            torch.as_tensor(ns, device=device))
+        G = self.t.shape[0]
+        # gap g joins inputs g and g+1 when both belong to the same process
+        self.same = self.proc[1:] == self.proc[:-1]
+        first = torch.ones(G, dtype=torch.bool, device=device)
+        first[1:] = ~self.same
+        self.first = first
+        flat = torch.arange(layout.band_elems, dtype=torch.int64)
+        self.index = torch.cat([layout.band_view(flat, i) for i in range(layout.count)], dim=1).to(device)
+        del flat
+        assert self.index.shape == (4, 2 * G), "every instance must be a process with l = 3 and N = 2 n"
+        self.N = float(2 * G)
+
+    def band(self, ells):
+        s2 = self.s2
+        lam_in = math.sqrt(3.0) / ells[self.proc]                        # per input
+        D = self.t[1:] - self.t[:-1]
+        lam = lam_in[1:]                                                 # per gap (the later input's process)
+        x = torch.where(self.same, lam * D, torch.ones_like(D))          # unused gaps get a harmless value
+        Dm = torch.where(self.same, D, torch.zeros_like(D))
+        e = torch.exp(-x)
+        q = torch.exp(-2.0 * x)
+        s00 = s2 * _bracket(x, _B_PLUS, 2.0)
+        s01 = 2.0 * s2 * lam * x * x * q
+        s11 = s2 * lam * lam * _bracket(x, _B_MINUS, -2.0)
+        # lower Cholesky factor of each input's conditional covariance:
+        # Pinf for the first input of a process, Sigma(gap before it) otherwise
+        f = self.first
+        pad = torch.zeros(1, dtype=D.dtype, device=D.device)
+        g00 = torch.cat([pad, torch.sqrt(s00)])
+        g10 = torch.cat([pad, s01 / torch.sqrt(s00)])
+        g11 = torch.cat([pad, torch.sqrt(s11 - (s01 * s01) / s00)])
+        one = torch.ones_like(lam_in)
+        c00 = torch.where(f, math.sqrt(s2) * one, g00)
+        c10 = torch.where(f, torch.zeros_like(lam_in), g10)
+        c11 = torch.where(f, lam_in * math.sqrt(s2), g11)
+        i00, i11 = 1.0 / c00, 1.0 / c11
+        i10 = -c10 / (c00 * c11)
+        # sub-diagonal block of the later input of gap g: -C^{-1} A(gap)
+        a00, a01, a10, a11 = e * (1.0 + x), e * Dm, -e * lam * x, e * (1.0 - x)
+        j00, j10, j11 = i00[1:], i10[1:], i11[1:]
+        z = torch.zeros_like(D)
+        o00 = torch.where(self.same, -(j00 * a00), z)
+        o01 = torch.where(self.same, -(j00 * a01), z)
+        o10 = torch.where(self.same, -(j10 * a00 + j11 * a10), z)
+        o11 = torch.where(self.same, -(j10 * a01 + j11 * a11), z)
+        G = self.t.shape[0]
+        vals = torch.zeros((4, 2 * G), dtype=torch.float64, device=self.device)
+        vals[0, 0::2] = i00
+        vals[0, 1::2] = i11
+        vals[1, 0::2] = i10
+        # block (k, k-1): entry (2k + a, 2k - 2 + c) on diagonal 2 + a - c, column 2(k-1) + c
+        vals[2, 0:2 * G - 2:2] = o00
+        vals[1, 1:2 * G - 2:2] = o01
+        vals[3, 0:2 * G - 2:2] = o10
+        vals[2, 1:2 * G - 2:2] = o11
+        pool = torch.zeros(self.layout.band_elems, dtype=torch.float64, device=self.device)
+        pool = pool.index_put((self.index.reshape(-1),), vals.reshape(-1))
+        return pool.to(self.layout.torch_dtype)
 
 
-def matern_M_band(layout, index, ts, ells, s2, device="cuda"):
-    """Band pool (lower bandwidth 3) holding M of every process, differentiable in
-    `ells` (a (count,) FP64 tensor).  Instance i is process i with N = 2 n_i."""
-    vals, idxs = [], []
-    for i in range(layout.count):
-        t = torch.as_tensor(ts[i], dtype=torch.float64, device=device)
-        (i00, i10, i11), (o00, o01, o10, o11) = matern_M_blocks(t, ells[i], s2)
-        n = t.shape[0]
-        N = 2 * n
-        rows = torch.zeros((4, N), dtype=torch.float64, device=device)
-        rows[0, 0::2] = i00
-        rows[0, 1::2] = i11
-        rows[1, 0::2] = i10
-        # block (k, k-1) at rows 2k, 2k+1 and columns 2k-2, 2k-1: entry (2k+a, 2k-2+c) on diagonal 2+a-c
-        rows[2, 0:N - 2:2] = o00                  # (a, c) = (0, 0)
-        rows[1, 1:N - 2:2] = o01                  # (0, 1)
-        rows[3, 0:N - 2:2] = o10                  # (1, 0)
-        rows[2, 1:N - 2:2] = o11                  # (1, 1)
-        vals.append(rows.reshape(-1))
-        idxs.append(index[i].reshape(-1).to(device))
-    pool = torch.zeros(layout.band_elems, dtype=torch.float64, device=device)
-    pool = pool.index_put((torch.cat(idxs),), torch.cat(vals))
-    return pool.to(layout.torch_dtype)
-
-
-def matern_kl(plan, index, ts, ells, s2, Lq, m, wsym, dmask):
+def matern_kl(plan, prior, ells, Lq, m, wsym, dmask):
     """sum_i KL(N(m_i, (Lq_i Lq_i^T)^{-1}) || N(0, Q_p,i^{-1})) (Eq. 5 / Alg. 7 with a
-    zero prior mean), with Q_p = M^T M built from (t_i, ell_i, s2):
+    zero prior mean), with Q_p = M^T M from `prior` (a MaternPrior):
 
       KL = 1/2 [ tr(Q_p band(Q_q^{-1})) + m^T Q_p m - N + log det Q_q - log det Q_p ],
 
     tr over lower storage (wsym), m^T Q_p m = |M m|^2 (matvec), log det Q_q =
     2 sum log Lq_ii and log det Q_p = 2 sum log M_ii (M is lower triangular).
     Differentiable in Lq, m and ells through the band operators' adjoints."""
-    lay = plan.layout
-    M = matern_M_band(lay, index, ts, ells, s2, device=Lq.device)
+    M = prior.band(ells)
     Qp = AG.product(plan, M, (3, 0), 1, M, (3, 0), 0, (3, 0))
     Sq = AG.subset_inverse(plan, Lq)
     trace = (wsym * Qp.to(torch.float64) * Sq.to(torch.float64)).sum()
@@ -171,5 +185,4 @@ def matern_kl(plan, index, ts, ells, s2, Lq, m, wsym, dmask):
     one = torch.ones((), dtype=Lq.dtype, device=Lq.device)
     logq = 2.0 * torch.log(torch.where(dmask, Lq, one).abs().to(torch.float64)).sum()
     logp = 2.0 * torch.log(torch.where(dmask, M, one).abs().to(torch.float64)).sum()
-    N = float(sum(2 * len(t) for t in ts))
-    return 0.5 * (trace + quad - N + logq - logp)
+    return 0.5 * (trace + quad - prior.N + logq - logp)

@@ -89,13 +89,13 @@ def matern_setup(count, n, dtype, panels=True, seed=W.BASE_SEED, min_gap=0.0):
     Lq = torch.tensor(lay.pack_band([rounded(p.Lq, dtype) for p in procs]), device="cuda", requires_grad=True)
     m = torch.tensor(lay.pack_rhs([rounded(p.m, dtype)[None] for p in procs]), device="cuda", requires_grad=True)
     ells = torch.tensor([p.lengthscale for p in procs], dtype=torch.float64, device="cuda", requires_grad=True)
-    ctx = dict(index=LS.band_index(lay), ts=[p.t for p in procs], wsym=LS.symmetric_weights(lay),
+    ctx = dict(prior=LS.MaternPrior(lay, [p.t for p in procs], 1.0), wsym=LS.symmetric_weights(lay),
                dmask=LS.diagonal_mask(lay))
     return procs, lay, plan, Lq, m, ells, ctx
 
 
 def gpu_kl(plan, ctx, ells, Lq, m):
-    return LS.matern_kl(plan, ctx["index"], ctx["ts"], ells, 1.0, Lq, m, ctx["wsym"], ctx["dmask"])
+    return LS.matern_kl(plan, ctx["prior"], ells, Lq, m, ctx["wsym"], ctx["dmask"])
 
 
 def oracle_kl(procs, dtype, ells=None, Lqs=None, ms=None):
