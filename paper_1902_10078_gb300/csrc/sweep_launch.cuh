@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "sweep_impl.cuh"
+#include "sweep_wide.cuh"
 
 namespace bnd {
 
@@ -135,6 +136,35 @@ staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
 template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
 constexpr size_t staged_smem_bytes() {
     return sizeof(T) * (size_t)StagedIOOf<T, L, K, FL, FWD, PANEL>::type::kWarpElems * kStagedWarpsPerBlock;
+}
+
+// ---------------------------------------------------------------------------
+// Wide-band kernel: one warp per chain of the generic bandwidth class (l = 0
+// or l above the register-window limit; such chains are whole instances).
+// ---------------------------------------------------------------------------
+constexpr int kWideWarpsPerBlock = 4;
+
+template <typename T, int K, int FL, bool FWD>
+__global__ void __launch_bounds__(kWarp * kWideWarpsPerBlock)
+wide_kernel(PlanDev P, SweepArgs<T> A, int64_t chain0, int64_t nchains) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+    const int lane = threadIdx.x % kWarp;
+    if (w >= nchains) return;
+    const Chain ch = P.chains[chain0 + w];
+    if (ch.inst < 0) return;
+    const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
+    if constexpr (FWD) run_fwd_wide<T, FL>(P, A, c, lane);
+    else run_bwd_wide<T, FL>(P, A, c, lane);
+}
+
+template <typename T, int K, int FL, bool FWD>
+static cudaError_t launch_wide(const bnd_plan *p, const SweepArgs<T> &A, int32_t t0, int32_t nt, cudaStream_t s) {
+    if (nt <= 0) return cudaSuccess;
+    const int64_t nch = (int64_t)nt * kWarp;
+    const int64_t blocks = (nch + kWideWarpsPerBlock - 1) / kWideWarpsPerBlock;
+    wide_kernel<T, K, FL, FWD><<<(unsigned)blocks, kWarp * kWideWarpsPerBlock, 0, s>>>(p->dev, A, (int64_t)t0 * kWarp,
+                                                                                       nch);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -309,7 +339,7 @@ static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cuda
             e = cudaStreamWaitEvent(side, p->ev_fork, 0);
             if (e != cudaSuccess) break;
             switch (c) {
-                case 0: e = launch_direct<T, K, FL, FWD>(p, A, p->class_task0[0], p->class_task0[1] - p->class_task0[0], side); break;
+                case 0: e = launch_wide<T, K, FL, FWD>(p, A, p->class_task0[0], p->class_task0[1] - p->class_task0[0], side); break;
                 case 1: e = launch_staged_l<T, 1, K, FL, FWD>(p, A, side); break;
                 case 2: e = launch_staged_l<T, 2, K, FL, FWD>(p, A, side); break;
                 case 3: e = launch_staged_l<T, 3, K, FL, FWD>(p, A, side); break;

@@ -176,3 +176,26 @@ def test_padding_never_read_nor_written(dtype, arr, tune):
         for c, r in enumerate(res):
             assert np.all(np.isfinite(arrs[c])), key
             assert_close(key, arrs[c], r[ref_key], tol[t])
+
+
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_wide_bands_warp_kernel(dtype, arr):
+    """Bandwidths above the register-window limit run one warp per instance
+    (lanes split the diagonals / window columns): the fused step agrees with
+    the oracle at l = 40, 64, 128."""
+    shapes = [(3000, 64), (1500, 128), (700, 40), (130, 128)]
+    insts, lay, plan = setup(shapes, 4, dtype, dict(seg_len=-1), arr=arr)
+    got = run_gmm(lay, plan, insts)
+    res, _ = O.batch_step(insts)
+    tol = TOL[dtype]
+    Lg, Sg, Qg = lay.unpack_band(got["L"]), lay.unpack_band(got["S"]), lay.unpack_band(got["Qb"])
+    Xg, Bg = lay.unpack_rhs(got["X"]), lay.unpack_rhs(got["Bb"])
+    for c, r in enumerate(res):
+        assert got["info"][c] == 0
+        assert_close("L", Lg[c], r["L"], tol["fwd"])
+        assert_close("S", Sg[c], r["S"], tol["fwd"])
+        assert_close("X", Xg[c], r["X"], tol["fwd"])
+        assert_close("Qbar", Qg[c], r["Qbar"], tol["grad"])
+        assert_close("Bbar", Bg[c], r["Bbar"], tol["grad"])
+        assert abs(got["logdet"][c] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))
