@@ -232,10 +232,6 @@ def run_ours(args, rank, world, device_index):
     torch.cuda.set_device(device_index)
     from paper_1902_10078_gb300 import build as bld
     bld.build()
-    tuning = dict(seg_len=args.seg_len, warmup=args.warm, flags=args.flags)
-    plan = BT.Plan(lay, tuning)
-    expect = B.LAYOUT_PANELS if panels else B.LAYOUT_ROWS
-    assert B.bnd_plan_layout(plan.handle) == expect, "the plan did not take the intended arrangement"
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     L, S, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool()
     X, Bb = lay.rhs_pool(), lay.rhs_pool()
@@ -243,6 +239,20 @@ def run_ours(args, rank, world, device_index):
     info = torch.empty(count, dtype=torch.int32, device="cuda")
     ldbar = torch.full((count,), 0.5, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    tuning = dict(seg_len=args.seg_len, warmup=args.warm, flags=args.flags)
+    autotuned = None
+    if args.autotune:
+        def make_step(pl):
+            def one():
+                B.banded_gmm_forward(pl.handle, dev["Q"], dev["B"], L, X, S, logdet, info)
+                B.banded_gmm_backward(pl.handle, L, X, S, dev["Xbar"], dev["Sbar"], ldbar, Qb, Bb)
+            return one
+        best, timings = BT.autotune(lay, make_step, use_cache=False)
+        tuning["seg_len"] = best["seg_len"]
+        autotuned = {"seg_len": best["seg_len"], "ms_per_candidate": timings}
+    plan = BT.Plan(lay, tuning)
+    expect = B.LAYOUT_PANELS if panels else B.LAYOUT_ROWS
+    assert B.bnd_plan_layout(plan.handle) == expect, "the plan did not take the intended arrangement"
 
     def fwd():
         B.banded_gmm_forward(plan.handle, dev["Q"], dev["B"], L, X, S, logdet, info)
@@ -351,6 +361,7 @@ def run_ours(args, rank, world, device_index):
     launches_per_step = 4 * (classes + (1 if plan.chains > count else 0))
     fwd_b, bwd_b, floor_b = algorithmic_bytes(lay)
     return dict(lay=lay, plan=plan, ms=ms, ms_e2e=ms_e2e, ms_fwd=ms_fwd, ms_bwd=ms_bwd, entries=entries,
+                autotuned=autotuned,
                 fwd_bytes=fwd_b, bwd_bytes=bwd_b, floor_bytes=floor_b, clocks=clk, h2d=h2d, d2h=d2h,
                 fixups=fixups, plain=plain, launches=launches_per_step * args.steps)
 
@@ -580,6 +591,8 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose the segment length by timing candidates on this batch first")
     ap.add_argument("--config", type=int, default=None, choices=[0, 1, 3, 4],
                     help="time another workload configuration instead of the uneven batch")
     ap.add_argument("--wide-ls", type=int, nargs="+", default=[64], help="bandwidths of --config 3")
@@ -668,6 +681,8 @@ def main():
         "clocks": r["clocks"],
         "cpu_baseline": cb,
     }
+    if r["autotuned"] is not None:
+        line["config"]["autotuned"] = r["autotuned"]
     if r["plain"] is not None:
         line["plain"] = r["plain"]
         line["batched_vs_plain"] = value / r["plain"]["value"]

@@ -179,3 +179,81 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Autotuning of the schedule
+# ---------------------------------------------------------------------------
+
+def workload_signature(layout) -> str:
+    """Key of a batch for the tuning cache: dtype, arrangement, k and a coarse
+    histogram of (bandwidth, log2 n) over the instances."""
+    import collections
+    import math
+    hist = collections.Counter((l, int(math.log2(max(n, 1)))) for n, l in zip(layout.ns, layout.ls))
+    parts = [f"dt{layout.dtype}", "panels" if layout.panels else "rows", f"k{layout.k}"]
+    parts += [f"l{l}n{b}x{c}" for (l, b), c in sorted(hist.items())]
+    return ";".join(parts)
+
+
+def _cache_path():
+    import os
+    return os.environ.get("BND_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "paper_1902_10078_gb300", "autotune.json"))
+
+
+def _cuda_timer(fn, reps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def autotune(layout, make_step, candidates=(256, 320, 384, 512, 768, 1024, 2048), reps=3, warmup=2,
+             use_cache=True, plan_factory=None, timer=None):
+    """Choose the segment length of a batch by timing one step per candidate.
+
+    `make_step(plan)` returns a callable that runs one step of the caller's
+    workload on `plan`.  Each candidate gets its own plan; the fastest
+    segment length is returned as a tuning dict (with the timings) and stored
+    in a JSON cache keyed by `workload_signature` (path: $BND_AUTOTUNE_CACHE,
+    default ~/.cache/paper_1902_10078_gb300/autotune.json), which later calls
+    consult first.  `plan_factory` and `timer` replace Plan construction and
+    CUDA-event timing (tests)."""
+    import json
+    import os
+    key = workload_signature(layout)
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return dict(seg_len=int(cache[key]["seg_len"])), cache[key].get("timings", {})
+    plan_factory = plan_factory or (lambda tuning: Plan(layout, tuning))
+    timer = timer or _cuda_timer
+    timings = {}
+    for seg in candidates:
+        plan = plan_factory(dict(seg_len=int(seg)))
+        try:
+            timings[str(seg)] = float(timer(make_step(plan), reps, warmup))
+        finally:
+            close = getattr(plan, "close", None)
+            if close:
+                close()
+    best = min(timings, key=timings.get)
+    if use_cache:
+        cache[key] = {"seg_len": int(best), "timings": timings}
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return dict(seg_len=int(best)), timings

@@ -1,0 +1,47 @@
+"""Schedule autotuner: candidate selection, signature and cache (host logic;
+plans and timings are replaced by fakes, so no GPU is needed)."""
+import json
+
+from paper_1902_10078_gb300 import batch as BT
+from paper_1902_10078_gb300 import binding as B
+
+
+class FakePlan:
+    def __init__(self, tuning):
+        self.tuning = tuning
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
+    monkeypatch.setenv("BND_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    lay = BT.Layout([5000, 6000, 300], [3, 3, 7], 4, B.BND_F32, panels=True)
+    made = []
+
+    def factory(tuning):
+        p = FakePlan(tuning)
+        made.append(p)
+        return p
+
+    cost = {256: 3.0, 384: 1.5, 512: 2.0}
+    tuning, timings = BT.autotune(lay, lambda plan: plan.tuning["seg_len"], candidates=(256, 384, 512),
+                                  plan_factory=factory, timer=lambda seg, reps, warmup: cost[seg])
+    assert tuning == {"seg_len": 384}
+    assert timings == {"256": 3.0, "384": 1.5, "512": 2.0}
+    assert all(p.closed for p in made) and len(made) == 3
+    stored = json.load(open(tmp_path / "tune.json"))
+    assert stored[BT.workload_signature(lay)]["seg_len"] == 384
+    # a second call is answered from the cache without building plans
+    tuning2, _ = BT.autotune(lay, lambda plan: None, plan_factory=lambda t: 1 / 0, timer=None)
+    assert tuning2 == {"seg_len": 384}
+
+
+def test_signature_separates_workloads():
+    a = BT.Layout([5000, 6000], [3, 3], 4, B.BND_F32, panels=True)
+    b = BT.Layout([5000, 6000], [3, 3], 4, B.BND_F32, panels=False)
+    c = BT.Layout([5000, 6000], [3, 5], 4, B.BND_F32, panels=True)
+    d = BT.Layout([5001, 6001], [3, 3], 4, B.BND_F32, panels=True)
+    assert len({BT.workload_signature(x) for x in (a, b, c)}) == 3
+    assert BT.workload_signature(a) == BT.workload_signature(d)     # same coarse histogram
