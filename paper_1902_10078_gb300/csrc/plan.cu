@@ -1,6 +1,8 @@
-// Host-side plan: validation, segmentation of long instances into chains,
-// grouping of equal-bandwidth chains into warp tasks, longest-first task
-// order, and the device workspace layout.
+// Host-side plan: validation, recognition of the batch's arrangement (rows,
+// 32-lane panels, general strides), segmentation of long instances into
+// chains, grouping of chains into warp tasks (equal-bandwidth chains for
+// rows; one (group, segment) per task for panels), longest-first task order,
+// and the device workspace layout.
 #include <algorithm>
 #include <climits>
 #include <cstdlib>

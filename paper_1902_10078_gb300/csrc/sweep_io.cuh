@@ -1,13 +1,18 @@
 // Stream I/O of the register-window sweeps.
 //
 // A sweep reads a fixed set of input streams and writes a fixed set of
-// output streams.  A stream is one contiguous row of a pool (a diagonal d of
-// a band operand, B'[d][*], or one right-hand-side column) read at column
-// j + off at iteration j.  Two implementations:
+// output streams.  A stream is one row of a pool (a diagonal d of a band
+// operand, B'[d][*], or one right-hand-side column) read at column j + off at
+// iteration j; consecutive columns are cs elements apart (1 for row plans,
+// 32 for panel plans).  Three implementations:
 //
 //  DirectIO : plain global loads / stores by the calling thread (used by the
-//             verify/fixup pass, which runs one chain per thread).
-//  StagedIO : per-lane shared-memory rings.  Each lane prefetches its own
+//             verify/fixup pass, which runs one chain per thread, and by the
+//             direct kernels of unaligned or general-stride batches).
+//  PanelIO  : panel plans; the warp's lanes are the 32 lanes of one instance
+//             group, so the warp stages each tile of a stream as one
+//             contiguous block (defined below).
+//  StagedIO : row plans; per-lane shared-memory rings.  Each lane prefetches its own
 //             chain's streams R tiles ahead with 16-byte cp.async copies
 //             (one 16-byte tile = TW columns), waits with per-iteration commit
 //             groups, and collects outputs in a tile buffer written back with

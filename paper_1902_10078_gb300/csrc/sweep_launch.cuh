@@ -1,6 +1,7 @@
-// Sweep kernels (staged per-bandwidth, persistent direct), the segment
-// verify/fixup kernel and their host launcher.  Included (once) by each
-// per-dtype, per-direction translation unit.
+// Sweep kernels (staged per-bandwidth for row and panel plans, one warp per
+// instance for wide bands, persistent direct), the segment verify/fixup
+// kernel and their host launcher.  Included (once) by each per-dtype,
+// per-direction translation unit.
 #pragma once
 
 #include <type_traits>
