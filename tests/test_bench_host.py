@@ -1,0 +1,56 @@
+"""Host-side pieces of bench.py: the algorithmic byte counts (the two-call
+floor of the uneven batch), the stored-traffic staleness rule and the ncu
+summary writer."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1902_10078_gb300 import batch as BT  # noqa: E402
+from paper_1902_10078_gb300 import binding as B  # noqa: E402
+
+
+def test_algorithmic_bytes_match_the_two_call_floor():
+    lay = BT.Layout([1000, 2000], [2, 7], 4, B.BND_F32)
+    fwd, bwd, floor = bench.algorithmic_bytes(lay)
+    w = 4
+    assert fwd + bwd == sum(w * n * (7 * (l + 1) + 5 * 4) for n, l in zip(lay.ns, lay.ls))
+    assert fwd == sum(w * n * (3 * (l + 1) + 2 * 4) for n, l in zip(lay.ns, lay.ls))
+    assert floor == sum(w * n * (4 * (l + 1) + 4 * 4) for n, l in zip(lay.ns, lay.ls))
+
+
+def test_stored_traffic_requires_matching_sources(tmp_path, monkeypatch):
+    f = tmp_path / "t.json"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.stored_traffic("banded_gmm_backward", 10) is None          # absent
+    f.write_text(json.dumps({"call": "banded_gmm_backward", "source_hash": bench.source_hash(),
+                             "dram_bytes_per_call": 200.0, "band_entries": 5}))
+    assert bench.stored_traffic("banded_gmm_backward", 10) == 400.0         # scaled by band entries
+    assert bench.stored_traffic("banded_gmm_forward", 10) is None           # another call
+    f.write_text(json.dumps({"call": "banded_gmm_backward", "source_hash": "0" * 16,
+                             "dram_bytes_per_call": 200.0, "band_entries": 5}))
+    assert bench.stored_traffic("banded_gmm_backward", 10) is None          # stale sources
+
+
+def test_summarize_ncu_sums_dram_bytes(tmp_path, monkeypatch):
+    out = tmp_path / "t.json"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(out))
+    csv = tmp_path / "c.csv"
+    hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"'
+    rows = ['"0","void k1(int)","dram__bytes_read.sum","Mbyte","1.5"',
+            '"0","void k1(int)","dram__bytes_write.sum","Kbyte","500"',
+            '"0","void k1(int)","gpu__time_duration.sum","usecond","10"',
+            '"1","void k2(int)","dram__bytes_read.sum","byte","1,000"']
+    csv.write_text("==PROF== note\n" + hdr + "\n" + "\n".join(rows) + "\n")
+
+    class A:
+        summarize_ncu = str(csv)
+        summarize_entries = 123
+        summarize_cmd = "cmd"
+    bench.summarize_ncu(A)
+    t = json.loads(out.read_text())
+    assert t["dram_bytes_per_call"] == 1.5e6 + 5e5 + 1000
+    assert t["launches"] == 2 and t["band_entries"] == 123 and t["source_hash"] == bench.source_hash()
