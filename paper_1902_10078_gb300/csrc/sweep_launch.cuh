@@ -95,49 +95,11 @@ __device__ __forceinline__ ChainCtx idle_ctx() {
     return c;
 }
 
-// ---------------------------------------------------------------------------
-// Staged kernel for one bandwidth L: block b runs warp tasks
-// [task0 + WPB b, task0 + WPB (b+1)) of the bandwidth's task range (ordered
-// longest first); each lane runs one chain.  Row plans stage every lane's own
-// rows (StagedIO); panel plans stage the group's interleaved columns with the
-// whole warp (PanelIO), so idle lanes stay in the loop.
-// ---------------------------------------------------------------------------
-template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
-struct StagedIOOf {
-    using SW = typename SweepOf<T, L, K, FL, FWD>::type;
-    using type = typename std::conditional<PANEL, PanelIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>,
-                                           StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>>::type;
-};
-
-template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
-__global__ void __launch_bounds__(kWarp * kStagedWarpsPerBlock)
-staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks) {
-    using IO = typename StagedIOOf<T, L, K, FL, FWD, PANEL>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    const int t = blockIdx.x * kStagedWarpsPerBlock + warp;
-    if (t >= ntasks) return;
-    const Task task = P.tasks[task0 + t];
-    const Chain ch = P.chains[(int64_t)task.chain0 + lane];
-    T *wsm = reinterpret_cast<T *>(smem_raw) + (size_t)warp * IO::kWarpElems;
-    if constexpr (PANEL) {
-        const ChainCtx c = ch.inst >= 0 ? make_ctx(P, ch.inst, ch.seg) : idle_ctx();
-        const ChainPtrs<T> ptrs = chain_ptrs(A, c);
-        IO io(ptrs, A, task, wsm, lane);
-        run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
-    } else {
-        if (ch.inst < 0) return;
-        const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
-        const ChainPtrs<T> ptrs = chain_ptrs(A, c);
-        IO io(ptrs, wsm, lane);
-        run_reg<T, L, K, FL, FWD>(P, A, c, RUN_COLD, nullptr, io);
-    }
-}
-
-template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
-constexpr size_t staged_smem_bytes() {
-    return sizeof(T) * (size_t)StagedIOOf<T, L, K, FL, FWD, PANEL>::type::kWarpElems * kStagedWarpsPerBlock;
-}
+// Staged per-bandwidth launcher: defined in sweep_staged.cuh and explicitly
+// instantiated per bandwidth in its own translation unit (sweep_staged_l*.cu),
+// so the large staged kernels compile in parallel.
+template <typename T, int L, int K, int FL, bool FWD>
+cudaError_t launch_staged_l(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Wide-band kernel: one warp per chain of the generic bandwidth class (l = 0
@@ -276,29 +238,6 @@ inline bool args_aligned16(const SweepArgs<T> &A) {
     return aligned16(A.Q) && aligned16(A.L) && aligned16(A.Lin) && aligned16(A.S) && aligned16(A.Sbar) &&
            aligned16(A.Sout) && aligned16(A.Lbar) && aligned16(A.Lbar_in) && aligned16(A.Qbar) &&
            aligned16(A.Bin) && aligned16(A.Xout) && aligned16(A.Xin) && aligned16(A.Ybar);
-}
-
-template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
-static cudaError_t launch_staged_lp(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
-    const int32_t t0 = p->class_task0[L], nt = p->class_task0[L + 1] - t0;
-    if (nt <= 0) return cudaSuccess;
-    constexpr size_t smem = staged_smem_bytes<T, L, K, FL, FWD, PANEL>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(staged_kernel<T, L, K, FL, FWD, PANEL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const unsigned blocks = (unsigned)((nt + kStagedWarpsPerBlock - 1) / kStagedWarpsPerBlock);
-    staged_kernel<T, L, K, FL, FWD, PANEL><<<blocks, kWarp * kStagedWarpsPerBlock, smem, s>>>(p->dev, A, t0, nt);
-    return cudaGetLastError();
-}
-
-template <typename T, int L, int K, int FL, bool FWD>
-static cudaError_t launch_staged_l(const bnd_plan *p, const SweepArgs<T> &A, cudaStream_t s) {
-    return p->layout == kLayoutPanels ? launch_staged_lp<T, L, K, FL, FWD, true>(p, A, s)
-                                      : launch_staged_lp<T, L, K, FL, FWD, false>(p, A, s);
 }
 
 template <typename T, int K, int FL, bool FWD>
