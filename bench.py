@@ -206,6 +206,18 @@ def summarize_ncu(args):
     print(json.dumps({k: out[k] for k in ("dram_bytes_per_call", "band_entries", "launches")}))
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank timings (every rank gets the result):
+    the slowest rank sets the job's time."""
+    import torch
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -346,11 +358,7 @@ def run_ours(args, rank, world, device_index):
     d2h = count * 8 + count * 4
 
     entries = int(sum(n * (l + 1) for n, l in zip(lay.ns, lay.ls)))
-    # max over ranks
-    t = torch.tensor([ms, ms_e2e, ms_fwd, ms_bwd], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, ms_e2e, ms_fwd, ms_bwd = [float(x) for x in t.tolist()]
+    ms, ms_e2e, ms_fwd, ms_bwd = max_over_ranks([ms, ms_e2e, ms_fwd, ms_bwd], world, "cuda")
 
     plain = None
     if args.plain and rank == 0:

@@ -76,3 +76,36 @@ def test_partition_small_cases():
     parts = shard.partition([3, 4], [1, 2], 4)
     assert sorted(sum(parts, [])) == [0, 1] and sum(1 for p in parts if not p) == 2
     assert sorted(shard.loads([3, 4], [1, 2], parts)) == [0, 0, 12, 36]
+
+
+def _timing_rank(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mine = [1.0 + rank, 5.0 - rank, 2.5, 10.0 * rank]
+        got = bench.max_over_ranks(mine, world, "cpu")
+        out.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_timings_take_the_slowest_rank():
+    """bench.py reports, on every rank, the element-wise maximum of the ranks'
+    timings (the job is as slow as its slowest rank)."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_timing_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert got[r] == [2.0, 5.0, 2.5, 10.0]
