@@ -9,11 +9,14 @@
  * code with the CUDA library (paper_1902_10078_gb300/csrc), and the CUDA
  * library never calls it.
  *
- * Every function works on ONE instance, written with the paper's dense (i, j)
- * indexing over band storage (App. B: the algorithms are stated densely but
- * touch only the band).  Loops follow the paper's order; there is no blocking,
- * no fusion and no reordering.  Floating-point contraction is disabled at
- * build time (-ffp-contract=off) so x86 and Arm builds give identical bits.
+ * Every function works on ONE instance, written with dense (i, j) indexing
+ * over band storage (the operators touch only the band).  The Cholesky and
+ * the solves follow the paper's row-by-row recurrences (Alg. 1, Sec. 4.1);
+ * the subset inverse is derived from the identity L^T Sigma = L^{-1}, and the
+ * two adjoints are the reverse mode of those recurrences, each written out
+ * with its derivation above the function.  There is no blocking and no
+ * fusion.  Floating-point contraction is disabled at build time
+ * (-ffp-contract=off) so x86 and Arm builds give identical bits.
  *
  * Storage (Sec. 4.3): a band matrix with lower/upper bandwidths (lo, up) is an
  * (lo+up+1) x n array B' with  B[i, j] = B'[up + i - j][j]  (0-based reading
@@ -24,17 +27,12 @@
  * Readings of the paper taken here (each one is listed in the design notes):
  *  - Alg. 1: the inner loop "j in max(i-l,0) to i+1" has an exclusive upper
  *    bound, so j runs up to and including i.
- *  - Alg. 2: the innermost loop "for l in j-1, in j_stop" re-uses the symbol
- *    l; it is read as k = j-1 down to j_stop inclusive.  The result Q_b is the
- *    gradient with respect to the LOWER stored entries of Q (each
- *    off-diagonal stored entry stands for Q_ij and Q_ji).
- *  - Alg. 3 and Alg. 4: the symbol l (and the undefined k of Alg. 4) in the
- *    slices U[i, i+1:i+l] and the loop bounds denote the band HEIGHT l+1,
- *    with exclusive slice ends; so m runs over i+1 .. i+l and i over
- *    j .. max(j-l, 0).
- *  - Alg. 4: "bS treated as symmetric" means the lower triangle starts with
- *    the upstream gradient of the stored entries and the upper triangle
- *    starts at zero; the algorithm itself moves gradient between the two.
+ *  - Cholesky adjoint (Alg. 2): Qbar is the gradient with respect to the
+ *    LOWER stored entries of Q (each off-diagonal stored entry stands for
+ *    Q_ij and Q_ji), because the factorisation reads only those.
+ *  - Subset-inverse adjoint (Alg. 4): Sbar is the gradient with respect to
+ *    the stored (lower) entries of S; each unordered pair {i, j} of the
+ *    symmetric Sigma is one variable whose adjoint starts at Sbar.
  *  - Table 1, solve with a vector: Lbar = -band_l(vbar s^T) where
  *    s = L^{-1} v and vbar = L^{-T} sbar (the appendix derivation drops the
  *    minus sign and writes u for ubar).
@@ -71,15 +69,15 @@ static void lb_zero(i64 n, int l, double *m, i64 ld)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 1 (App. B): Cholesky of a banded SPD matrix, row by row.             */
+/* Cholesky C (Sec. 4.1, Alg. 1) of a banded SPD matrix, row by row.         */
 /* ------------------------------------------------------------------------ */
 int orc_cholesky(i64 n, int l, const double *Q, i64 ldq, double *L, i64 ldl)
 {
-    lb_zero(n, l, L, ldl);                       /* "Initialize L with zeros" */
+    lb_zero(n, l, L, ldl);
     for (i64 i = 0; i < n; ++i) {
         for (i64 j = imax(i - l, 0); j <= i; ++j) {
             i64 m = imax(imax(i - l, j - l), 0);
-            double s = 0.0;                      /* s = sum(L[i, m:j] * L[j, m:j]) */
+            double s = 0.0;                      /* inner product of rows i and j of L left of column j */
             for (i64 t = m; t < j; ++t) s += LB(L, ldl, i, t) * LB(L, ldl, j, t);
             if (i == j) {
                 double piv = LB(Q, ldq, i, i) - s;
@@ -134,127 +132,122 @@ void orc_solve(i64 n, int l, const double *L, i64 ldl, int trans, int k,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 3 (App. B): lower band of (L L^T)^{-1} from L (Takahashi).           */
-/* Sym is a symmetric band with both bandwidths l: general storage, up = l.  */
+/* Subset inverse I (Sec. 4.1, Alg. 3): S = lower band of Sigma = (L L^T)^-1. */
+/*                                                                           */
+/* Derived from Sigma = L^{-T} L^{-1}, i.e. L^T Sigma = L^{-1}.  L^{-1} is   */
+/* lower triangular with diagonal 1 / L_ii, so entry (i, j), j >= i, of      */
+/* L^T Sigma = L^{-1} reads                                                  */
+/*     L_ii Sigma_ij + sum_{k=i+1}^{i+l} L_ki Sigma_kj = [i == j] / L_ii,     */
+/* which gives Sigma_ij from entries of rows below i.  Rows are taken from   */
+/* the last one up; inside row i the off-diagonal entries j = i+l .. i+1     */
+/* first (they use only rows below i), then the diagonal (it uses them).    */
+/* Every Sigma_kj referenced has |k - j| <= l, so only the band is needed;   */
+/* the symmetric entry (k, j) with k < j is read as (j, k).                  */
 /* ------------------------------------------------------------------------ */
 void orc_subset_inverse(i64 n, int l, const double *L, i64 ldl, double *S, i64 lds)
 {
-    i64 ldw = n;
-    double *Sym = (double *)calloc((size_t)(2 * l + 1) * (size_t)ldw, sizeof(double));
-    double *vec = (double *)malloc((size_t)n * sizeof(double));
-    double *U = (double *)calloc((size_t)(l + 1) * (size_t)ldw, sizeof(double)); /* U[i, i+e] at U[e*ldw + i] */
-    for (i64 i = 0; i < n; ++i) vec[i] = LB(L, ldl, i, i);          /* vec = diag(L) */
-    for (i64 i = 0; i < n; ++i)                                       /* U = transpose(L / vec) */
-        for (i64 m = i; m <= imin(i + l, n - 1); ++m)
-            U[(size_t)(m - i) * ldw + i] = LB(L, ldl, m, i) / vec[i];
-#define UU(i, m) U[(size_t)((m) - (i)) * ldw + (i)]
-#define SY(i, j) GB(Sym, ldw, l, i, j)
-    for (i64 j = n - 1; j >= 0; --j) {
-        for (i64 i = j; i >= imax(j - l, 0); --i) {
-            double s = 0.0;                   /* sum(U[i, i+1:i+k] Sym[i+1:i+k, j]), k = l+1 */
-            for (i64 m = i + 1; m <= imin(i + l, n - 1); ++m) s += UU(i, m) * SY(m, j);
-            SY(i, j) = -s;
-            SY(j, i) = SY(i, j);
-            if (i == j) SY(i, i) += 1.0 / (vec[i] * vec[i]);
+#define SIG(a, b) ((a) >= (b) ? LB(S, lds, a, b) : LB(S, lds, b, a))
+    lb_zero(n, l, S, lds);
+    for (i64 i = n - 1; i >= 0; --i) {
+        i64 last = imin(i + l, n - 1);
+        double lii = LB(L, ldl, i, i);
+        for (i64 j = last; j >= i; --j) {
+            double acc = (j == i) ? 1.0 / lii : 0.0;
+            for (i64 k = i + 1; k <= last; ++k) acc -= LB(L, ldl, k, i) * SIG(k, j);
+            LB(S, lds, j, i) = acc / lii;
         }
     }
-    lb_zero(n, l, S, lds);                    /* S = lower_band(Sym) */
-    for (i64 j = 0; j < n; ++j)
-        for (i64 i = j; i <= imin(j + l, n - 1); ++i) LB(S, lds, i, j) = SY(i, j);
-#undef UU
-#undef SY
-    free(Sym); free(vec); free(U);
+#undef SIG
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2 (App. B): reverse mode of Alg. 1.  Lbar is copied (the algorithm   */
-/* updates it in place); Qbar is the gradient w.r.t. the lower stored        */
-/* entries of Q.                                                             */
+/* Reverse mode of the Cholesky (Alg. 2), derived by differentiating the     */
+/* entries of L as functions of Q.  Forward, column by column:               */
+/*     a_ij = Q_ij - sum_{k=max(i-l,0)}^{j-1} L_ik L_jk      (j <= i <= j+l)   */
+/*     L_jj = sqrt(a_jj),   L_ij = a_ij / L_jj  (i > j).                     */
+/* The adjoints are taken in the exact reverse order: columns from the last  */
+/* one down, inside a column the off-diagonal entries from the bottom up,    */
+/* then the diagonal (which every off-diagonal entry of its column uses):    */
+/*     abar_ij = Lbar_ij / L_jj;  Lbar_jj -= abar_ij L_ij          (i > j)   */
+/*     abar_jj = Lbar_jj / (2 L_jj)                                          */
+/*     Qbar_ij = abar_ij;  for each k in the sum:                            */
+/*         Lbar_ik -= abar_ij L_jk,  Lbar_jk -= abar_ij L_ik                  */
+/* (for i = j both updates hit Lbar_jk).  The forward reads only the lower   */
+/* entries of Q, so Qbar is the gradient w.r.t. the LOWER stored entries     */
+/* (an off-diagonal stored entry stands for Q_ij and Q_ji).  Lbar is copied. */
 /* ------------------------------------------------------------------------ */
 void orc_cholesky_vjp(i64 n, int l, const double *L, i64 ldl, const double *Lbar, i64 ldlb,
                       double *Qbar, i64 ldqb)
 {
-    double *Lb = (double *)malloc((size_t)(l + 1) * (size_t)n * sizeof(double));
+    double *G = (double *)malloc((size_t)(l + 1) * (size_t)n * sizeof(double));   /* running Lbar */
     for (int d = 0; d <= l; ++d)
-        for (i64 j = 0; j < n; ++j) Lb[(size_t)d * n + j] = (j + d < n) ? Lbar[(size_t)d * ldlb + j] : 0.0;
-    lb_zero(n, l, Qbar, ldqb);                       /* "Initialize Q_b with zeros" */
-    for (i64 i = n - 1; i >= 0; --i) {
-        i64 jstop = imax(i - l, 0);
-        for (i64 j = i; j >= jstop; --j) {
-            if (j == i) {
-                LB(Qbar, ldqb, i, i) = 0.5 * LB(Lb, n, i, i) / LB(L, ldl, i, i);
+        for (i64 j = 0; j < n; ++j) G[(size_t)d * n + j] = (j + d < n) ? Lbar[(size_t)d * ldlb + j] : 0.0;
+    lb_zero(n, l, Qbar, ldqb);
+    for (i64 j = n - 1; j >= 0; --j) {
+        double ljj = LB(L, ldl, j, j);
+        for (i64 i = imin(j + l, n - 1); i >= j; --i) {
+            double abar;
+            if (i > j) {
+                abar = LB(G, n, i, j) / ljj;
+                LB(G, n, j, j) -= abar * LB(L, ldl, i, j);
             } else {
-                LB(Qbar, ldqb, i, j) = LB(Lb, n, i, j) / LB(L, ldl, j, j);
-                LB(Lb, n, j, j) -= LB(Lb, n, i, j) * LB(L, ldl, i, j) / LB(L, ldl, j, j);
+                abar = LB(G, n, j, j) / (2.0 * ljj);
             }
-            for (i64 k = j - 1; k >= jstop; --k) {
-                LB(Lb, n, i, k) -= LB(Qbar, ldqb, i, j) * LB(L, ldl, j, k);
-                LB(Lb, n, j, k) -= LB(Qbar, ldqb, i, j) * LB(L, ldl, i, k);
+            LB(Qbar, ldqb, i, j) = abar;
+            for (i64 k = imax(i - l, 0); k < j; ++k) {
+                LB(G, n, i, k) -= abar * LB(L, ldl, j, k);
+                LB(G, n, j, k) -= abar * LB(L, ldl, i, k);
             }
         }
     }
-    free(Lb);
+    free(G);
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 4 (App. B): reverse mode of Alg. 3.  Output Lbar (lower band) is the  */
-/* gradient w.r.t. the stored entries of L; accumulate = 1 adds into Lbar.   */
+/* Reverse mode of the subset inverse (Alg. 4), derived by differentiating   */
+/* the recursion of orc_subset_inverse above.  Each unordered pair {i, j}    */
+/* of Sigma is one variable, so its adjoint sits on the stored entry (the    */
+/* lower one) and starts as Sbar.  With t_ij = sum_{k=i+1}^{i+l} L_ki Sigma_kj: */
+/*     Sigma_ij = -t_ij / L_ii                         (j > i)                */
+/*     Sigma_ii = 1 / L_ii^2 - t_ii / L_ii                                   */
+/* so, for g = Sigma-bar_ij:                                                 */
+/*     Lbar_ii += g (t_ij / L_ii^2)            (j > i)                       */
+/*     Lbar_ii += g (-2 / L_ii^3 + t_ii / L_ii^2)   (j = i)                   */
+/*     Lbar_ki -= g Sigma_kj / L_ii,   Sigma-bar_kj -= g L_ki / L_ii          */
+/* The forward takes rows from the last up and, in a row, the diagonal       */
+/* last; the reverse takes rows from the first down and, in a row, the       */
+/* diagonal first.  Row i only feeds adjoints of pairs whose smaller index  */
+/* is > i, or of its own off-diagonal pairs (through the diagonal), so every */
+/* adjoint is complete when it is consumed.  Sigma is read from S (the       */
+/* forward output).  accumulate = 1 adds into Lbar.                          */
 /* ------------------------------------------------------------------------ */
 void orc_subset_inverse_vjp(i64 n, int l, const double *L, i64 ldl, const double *S, i64 lds,
                             const double *Sbar, i64 ldsb, double *Lbar, i64 ldlb, int accumulate)
 {
-    i64 ldw = n;
-    double *bS = (double *)calloc((size_t)(2 * l + 1) * (size_t)ldw, sizeof(double));
-    double *bU = (double *)calloc((size_t)(l + 1) * (size_t)ldw, sizeof(double)); /* bU[i, i+e] at e*ldw+i */
-    double *U = (double *)calloc((size_t)(l + 1) * (size_t)ldw, sizeof(double));
-    double *vec = (double *)malloc((size_t)n * sizeof(double));
-    double *bvec_inv_2 = (double *)calloc((size_t)n, sizeof(double));
-    double *bvec = (double *)malloc((size_t)n * sizeof(double));
-#define SYM(i, j) ((i) >= (j) ? LB(S, lds, i, j) : LB(S, lds, j, i))
-#define BS(i, j) GB(bS, ldw, l, i, j)
-#define UU(i, m) U[(size_t)((m) - (i)) * ldw + (i)]
-#define BU(i, m) bU[(size_t)((m) - (i)) * ldw + (i)]
-    /* bS: lower triangle holds Sbar on the stored entries, upper starts at 0. */
-    for (i64 j = 0; j < n; ++j)
-        for (i64 i = j; i <= imin(j + l, n - 1); ++i) BS(i, j) = LB(Sbar, ldsb, i, j);
-    for (i64 i = 0; i < n; ++i) vec[i] = LB(L, ldl, i, i);          /* vec = diag(L) */
-    for (i64 i = 0; i < n; ++i)                                       /* U = transpose(L / vec) */
-        for (i64 m = i; m <= imin(i + l, n - 1); ++m) UU(i, m) = LB(L, ldl, m, i) / vec[i];
-
-    for (i64 j = 0; j < n; ++j) {
-        for (i64 i = imax(0, j - l); i <= j; ++i) {
-            if (i == j) bvec_inv_2[i] += BS(i, i);
-            /* grad of Sym[j, i] = Sym[i, j] */
-            double tmp = BS(j, i);
-            BS(j, i) = 0.0;
-            BS(i, j) += tmp;
-            /* grad of Sym[i, j] = -sum(U[i, i+1:i+k] Sym[i+1:i+k, j]) */
-            for (i64 m = i + 1; m <= imin(i + l, n - 1); ++m) {
-                BU(i, m) -= SYM(m, j) * BS(i, j);
-                BS(m, j) -= UU(i, m) * BS(i, j);
+    double *G = (double *)calloc((size_t)(l + 1) * (size_t)n, sizeof(double));   /* pair adjoints */
+#define SIG(a, b) ((a) >= (b) ? LB(S, lds, a, b) : LB(S, lds, b, a))
+#define GP(a, b) (*((a) >= (b) ? &LB(G, n, a, b) : &LB(G, n, b, a)))
+    for (int d = 0; d <= l; ++d)
+        for (i64 j = 0; j + d < n; ++j) G[(size_t)d * n + j] = Sbar[(size_t)d * ldsb + j];
+    if (!accumulate) lb_zero(n, l, Lbar, ldlb);
+    for (i64 i = 0; i < n; ++i) {
+        i64 last = imin(i + l, n - 1);
+        double lii = LB(L, ldl, i, i);
+        for (i64 j = i; j <= last; ++j) {
+            double g = GP(j, i);
+            double t = 0.0;
+            for (i64 k = i + 1; k <= last; ++k) t += LB(L, ldl, k, i) * SIG(k, j);
+            if (j == i) LB(Lbar, ldlb, i, i) += g * (-2.0 / (lii * lii * lii) + t / (lii * lii));
+            else        LB(Lbar, ldlb, i, i) += g * t / (lii * lii);
+            for (i64 k = i + 1; k <= last; ++k) {
+                LB(Lbar, ldlb, k, i) -= g * SIG(k, j) / lii;
+                GP(k, j) -= g * LB(L, ldl, k, i) / lii;
             }
-            BS(i, j) = 0.0;
         }
     }
-    /* grad of U = transpose(L / vec):  bL = transpose(bU) / vec */
-    if (!accumulate) lb_zero(n, l, Lbar, ldlb);
-    for (i64 i = 0; i < n; ++i)
-        for (i64 m = i + 1; m <= imin(i + l, n - 1); ++m) LB(Lbar, ldlb, m, i) += BU(i, m) / vec[i];
-    /* grad of 1 / vec^2 */
-    for (i64 i = 0; i < n; ++i) bvec[i] = -2.0 * bvec_inv_2[i] / (vec[i] * vec[i] * vec[i]);
-    /* grad of 1 / vec:  bvec -= sum(transpose(bU) * L, 0) / vec^2 */
-    for (i64 i = 0; i < n; ++i) {
-        double s = 0.0;
-        for (i64 m = i; m <= imin(i + l, n - 1); ++m) s += BU(i, m) * LB(L, ldl, m, i);
-        bvec[i] -= s / (vec[i] * vec[i]);
-    }
-    /* grad of vec = diag(L) */
-    for (i64 i = 0; i < n; ++i) LB(Lbar, ldlb, i, i) += bvec[i];
-#undef SYM
-#undef BS
-#undef UU
-#undef BU
-    free(bS); free(bU); free(U); free(vec); free(bvec_inv_2); free(bvec);
+#undef SIG
+#undef GP
+    free(G);
 }
 
 /* ------------------------------------------------------------------------ */
