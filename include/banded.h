@@ -213,8 +213,10 @@ bnd_status banded_subset_inverse_vjp(const bnd_plan *plan, const void *L, const 
  *             of Q) and Bbar (nullable) of
  *             <Xbar, X> + <Sbar, S> + sum_i ldbar_i * logdet_i,
  *             composed per Table 1, Alg. 2 and Alg. 4.
- * Needs k in {1, 2, 3, 4}.  The forward writes L, X, S (and keeps L^{-1} B in
- * the workspace); the backward reads L, X, S.
+ * Needs a plan with k in {1, 2, 3, 4} (BND_EINVAL otherwise): the fused
+ * sweeps carry at most 4 right-hand sides; plans with more columns use the
+ * separate operators.  The forward writes L, X, S (and keeps L^{-1} B in the
+ * workspace); the backward reads L, X, S.
  * ------------------------------------------------------------------------- */
 bnd_status banded_gmm_forward(const bnd_plan *plan, const void *Q, const void *B, void *L, void *X,
                               void *S, double *logdet, int32_t *info, void *stream);
@@ -259,7 +261,8 @@ bnd_status banded_product_vjp(const bnd_plan *plan, const void *A, int32_t alo, 
  *
  *   x = (L L^T)^{-1} b   for ONE instance (order n, lower bandwidth l) and one
  *   right-hand side; L (lower band, row stride ld >= n), b and x are DEVICE
- *   pointers, b and x hold n elements and must not alias.
+ *   pointers, b and x hold n elements.  x may share no byte with b or with
+ *   L's (l ld + n)-element region (BND_EINVAL otherwise).
  *
  * No plan and no workspace: the intermediate y = L^{-1} b lives in a fixed
  * 16 MiB device array inside the library (n <= 4,194,304 in FP32,
@@ -268,7 +271,9 @@ bnd_status banded_product_vjp(const bnd_plan *plan, const void *A, int32_t alo, 
  * nothing (no cudaMalloc / cudaFree, no allocating library routine).
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
- *    stream capture.
+ *    stream capture.  The address is kept for the life of the process: after
+ *    cudaDeviceReset the library has to be reloaded before this call is used
+ *    again.
  *  - All calls on a device share that device's array, which keeps the last
  *    call's contents (nothing in it needs to start at zero).  Calls that
  *    overlap on the same GPU (e.g. issued on two streams) race on it: order

@@ -21,7 +21,9 @@ constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of g_noalloc_scratch, looked up once per device (in host code
-// the symbol itself is only a host-side stand-in, not a device address).
+// the symbol itself is only a host-side stand-in, not a device address).  The
+// address stays valid for the life of the device's primary context; after a
+// cudaDeviceReset the library must be reloaded (the cached address is stale).
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
@@ -99,12 +101,24 @@ static bnd_status noalloc_solve_t(int64_t n, int32_t l, const void *Lm, int64_t 
 
 }  // namespace bnd
 
+namespace {
+// Byte ranges [p, p + bytes) that share at least one byte.
+bool overlap(const void *p, size_t pb, const void *q, size_t qb) {
+    const uintptr_t a = (uintptr_t)p, c = (uintptr_t)q;
+    return a < c + qb && c < a + pb;
+}
+}  // namespace
+
 extern "C" bnd_status banded_solve_precision_noalloc(bnd_dtype dtype, int64_t n, int32_t l, const void *L, int64_t ld,
                                                      const void *b, void *x, void *stream) {
     if (dtype != BND_F32 && dtype != BND_F64) return BND_EINVAL;
-    if (n < 1 || l < 0 || l > 1024 || ld < n || !L || !b || !x || b == x) return BND_EINVAL;
+    if (n < 1 || l < 0 || l > 1024 || ld < n || !L || !b || !x) return BND_EINVAL;
     const size_t esz = dtype == BND_F32 ? 4 : 8;
     if (((uintptr_t)L % esz) || ((uintptr_t)b % esz) || ((uintptr_t)x % esz)) return BND_EALIGN;
+    // x is written while b and L are still being read: it may share no byte with either
+    // (b and L may overlap each other: both are only read)
+    const size_t vec_bytes = (size_t)n * esz, band_bytes = ((size_t)l * (size_t)ld + (size_t)n) * esz;
+    if (overlap(x, vec_bytes, b, vec_bytes) || overlap(x, vec_bytes, L, band_bytes)) return BND_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return dtype == BND_F32 ? bnd::noalloc_solve_t<float>(n, l, L, ld, b, x, s)
                             : bnd::noalloc_solve_t<double>(n, l, L, ld, b, x, s);

@@ -4,6 +4,7 @@
 // per-direction translation unit.
 #pragma once
 
+#include <mutex>
 #include <type_traits>
 
 #include "sweep_impl.cuh"
@@ -21,6 +22,25 @@ namespace bnd {
 #define BND_RING_LARGE_L 2
 #endif
 constexpr int kStagedWarpsPerBlock = BND_STAGED_WPB;
+
+// One-time per-device values (kernel occupancy, function attributes set on a
+// device).  Each caller keeps one slot table per kernel; the first launch on a
+// device fills that device's slot under the table's mutex, so two host
+// threads or two devices never see a half-written or foreign value.  A
+// failed computation (value <= 0) is not cached.
+constexpr int kMaxDevices = 64;
+struct PerDeviceSlots {
+    std::mutex mu;
+    int value[kMaxDevices] = {};
+};
+template <class F>
+inline int per_device(PerDeviceSlots &t, F compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute();
+    std::lock_guard<std::mutex> lock(t.mu);
+    if (t.value[dev] <= 0) t.value[dev] = compute();
+    return t.value[dev];
+}
 
 // Ring depth (tiles per stream) of the staged kernels: short iterations
 // (small l) want a deeper prefetch to cover the memory latency, long ones
@@ -243,16 +263,18 @@ inline bool args_aligned16(const SweepArgs<T> &A) {
 template <typename T, int K, int FL, bool FWD>
 static cudaError_t launch_direct(const bnd_plan *p, const SweepArgs<T> &A, int32_t t0, int32_t nt, cudaStream_t s) {
     if (nt <= 0) return cudaSuccess;
-    static int blocks_per_sm = -1;
-    static int num_sms = 0;
-    if (blocks_per_sm < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    static PerDeviceSlots occ, sms;
+    const int blocks_per_sm = per_device(occ, [] {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<T, K, FL, FWD>, 128, 0);
-        blocks_per_sm = b > 0 ? b : 1;
-    }
+        return b > 0 ? b : 1;
+    });
+    const int num_sms = per_device(sms, [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v;
+    });
     const int bps = p->blocks_per_sm > 0 ? p->blocks_per_sm : blocks_per_sm;
     int64_t blocks = (int64_t)num_sms * bps;
     const int64_t need = (nt + 3) / 4;

@@ -56,13 +56,12 @@ static cudaError_t launch_staged_lp(const bnd_plan *p, const SweepArgs<T> &A, cu
     const int32_t t0 = p->class_task0[L], nt = p->class_task0[L + 1] - t0;
     if (nt <= 0) return cudaSuccess;
     constexpr size_t smem = staged_smem_bytes<T, L, K, FL, FWD, PANEL>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(staged_kernel<T, L, K, FL, FWD, PANEL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static PerDeviceSlots attr;       // the attribute is set once on every device the kernel runs on
+    const int ok = per_device(attr, [] {
+        return cudaFuncSetAttribute(staged_kernel<T, L, K, FL, FWD, PANEL>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess ? 1 : -1;
+    });
+    if (ok <= 0) return cudaErrorInvalidValue;
     const unsigned blocks = (unsigned)((nt + kStagedWarpsPerBlock - 1) / kStagedWarpsPerBlock);
     staged_kernel<T, L, K, FL, FWD, PANEL><<<blocks, kWarp * kStagedWarpsPerBlock, smem, s>>>(p->dev, A, t0, nt);
     return cudaGetLastError();

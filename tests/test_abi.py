@@ -159,3 +159,34 @@ def test_plan_rejects_bad_strides(lib, bad):
     with pytest.raises(B.BandedError) as e:
         B.bnd_plan_create(B.BND_F32, [d], 1)
     assert e.value.status == 1
+
+
+# The allocation-free solve validates its pointers on the host before any CUDA
+# call: every case below is rejected there (fake addresses are never used).
+_BASE = 1 << 40
+
+
+@pytest.mark.parametrize("x_off,b_off,why", [
+    (0, 0, "x is b"),
+    (8 * 10, 8 * 50, "x overlaps the tail of b"),
+    (8 * 90, 8 * 50, "x overlaps the head of b"),
+    (8 * 300, 8 * 1000, "x overlaps L"),
+])
+def test_noalloc_rejects_overlapping_output(lib, x_off, b_off, why):
+    n, l, ld = 100, 2, 128
+    L = _BASE
+    b = _BASE + (1 << 20) + b_off if why != "x overlaps L" else _BASE + (1 << 20)
+    x = (_BASE + (1 << 20) + x_off) if why != "x overlaps L" else _BASE + x_off
+    with pytest.raises(B.BandedError) as e:
+        B.banded_solve_precision_noalloc(B.BND_F64, n, l, L, ld, b, x, stream=0)
+    assert e.value.status == 1, why
+
+
+def test_noalloc_rejects_misaligned_and_bad_sizes(lib):
+    with pytest.raises(B.BandedError) as e:
+        B.banded_solve_precision_noalloc(B.BND_F64, 10, 2, _BASE + 4, 16, _BASE + 4096, _BASE + 8192, stream=0)
+    assert e.value.status == 5
+    for n, l, ld in ((0, 1, 8), (10, -1, 16), (10, 2, 9)):
+        with pytest.raises(B.BandedError) as e:
+            B.banded_solve_precision_noalloc(B.BND_F64, n, l, _BASE, ld, _BASE + 4096, _BASE + 8192, stream=0)
+        assert e.value.status == 1
