@@ -45,43 +45,27 @@ WORKLOAD = "uneven batch: 4096 instances, n log-uniform [1000, 65536], l in {1,2
 
 # --------------------------------------------------------------------------- inputs
 
-def _fill_worker(args):
-    """Generate instances [i0, i1); return their band / RHS arrays."""
-    i0, i1, seed, ns, ls, k = args
-    out = []
-    for i in range(i0, i1):
-        ins = W.make_instance(ns[i], ls[i], k, seed + i)
-        out.append((i, ins.Q.astype(np.float32), ins.Sbar.astype(np.float32), ins.B.astype(np.float32),
-                    ins.Xbar.astype(np.float32)))
-    return out
+def batch_layout(count, k, ls, panels, rank=0):
+    """The uneven batch of `rank`: its pool layout and every slot's seed.
+
+    Instance i (original order) has the i-th drawn shape and seed
+    BASE_SEED + rank * count + i; a panel layout reorders the instances
+    (panel_order) and carries each one's seed along, so slot p holds original
+    instance order[p] whatever the arrangement."""
+    from paper_1902_10078_gb300 import batch as BT
+    from paper_1902_10078_gb300 import binding as B
+    ns, lss = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919, ls=ls)
+    order = BT.panel_order(ns, lss) if panels else list(range(count))
+    lay = BT.Layout([int(ns[i]) for i in order], [int(lss[i]) for i in order], k, B.BND_F32, panels=panels)
+    seeds = [W.BASE_SEED + rank * count + int(i) for i in order]
+    return lay, seeds, order
 
 
-def generate(lay, seed, workers):
-    """Host pools Q, Sbar (band) and B, Xbar (RHS) in the layout's arrangement,
-    generated by a spawn pool (started before any CUDA use) over chunks of
-    instances and packed through the layout's per-instance views."""
-    import multiprocessing as mp
-    pools = {"Q": np.zeros(lay.band_elems, np.float32), "Sbar": np.zeros(lay.band_elems, np.float32),
-             "B": np.zeros(lay.rhs_elems, np.float32), "Xbar": np.zeros(lay.rhs_elems, np.float32)}
-    chunks = max(1, min(workers * 4, lay.count))
-    bounds = np.linspace(0, lay.count, chunks + 1).astype(int)
-    jobs = [(int(bounds[c]), int(bounds[c + 1]), seed, lay.ns, lay.ls, lay.k)
-            for c in range(chunks) if bounds[c + 1] > bounds[c]]
-
-    def put(res):
-        for i, q, sb, b, xb in res:
-            lay.band_view(pools["Q"], i)[: q.shape[0]] = q
-            lay.band_view(pools["Sbar"], i)[: sb.shape[0]] = sb
-            lay.rhs_view(pools["B"], i)[: b.shape[0]] = b
-            lay.rhs_view(pools["Xbar"], i)[: xb.shape[0]] = xb
-    if workers > 1:
-        with mp.get_context("spawn").Pool(workers) as pool:
-            for res in pool.imap_unordered(_fill_worker, jobs):
-                put(res)
-    else:
-        for j in jobs:
-            put(_fill_worker(j))
-    return pools
+def cpu_sample(count, size):
+    """Original indices of the bounded sample the oracle runs (the same instances
+    in the CPU baseline, the reference arm and the parity check of the GPU run)."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    return np.sort(rng.choice(count, size=min(size, count), replace=False))
 
 
 # --------------------------------------------------------------------------- clocks
@@ -98,7 +82,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -234,13 +218,9 @@ def run_ours(args, rank, world, device_index):
     from paper_1902_10078_gb300 import binding as B
 
     count = args.count
-    ns, ls = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919, ls=tuple(int(x) for x in args.ls.split(",")))
     panels = args.layout == "panels"
-    if panels:       # the same instances, ordered so that panel groups are full and even
-        order = BT.panel_order(ns, ls)
-        ns, ls = [ns[i] for i in order], [ls[i] for i in order]
-    lay = BT.Layout(ns, ls, args.k, B.BND_F32, panels=panels)
-    host = generate(lay, W.BASE_SEED + rank * count, args.workers)      # before any CUDA use
+    lay, seeds, order = batch_layout(count, args.k, tuple(int(x) for x in args.ls.split(",")), panels, rank)
+    host = W.fill_pools(lay, seeds, args.workers)
     torch.cuda.set_device(device_index)
     from paper_1902_10078_gb300 import build as bld
     bld.build()
@@ -332,17 +312,18 @@ def run_ours(args, rank, world, device_index):
     ms_fwd = timed(fwd, max(2, args.steps // 2))
     ms_bwd = timed(bwd, max(2, args.steps // 2))
 
-    # end to end: pinned host inputs -> device, step, log-dets back to the host
+    # end to end: pinned host inputs -> device, step, the step's results back to pinned host
+    # buffers (forward X, S and log-dets with info; backward Qbar and Bbar)
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-    ld_host = torch.empty(count, dtype=torch.float64).pin_memory()
-    info_host = torch.empty(count, dtype=torch.int32).pin_memory()
+    results = {"X": X, "S": S, "Qbar": Qb, "Bbar": Bb, "logdet": logdet, "info": info}
+    back = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in results.items()}
 
     def e2e_step():
         for k in ("Q", "B", "Xbar", "Sbar"):
             dev[k].copy_(pinned[k], non_blocking=True)
         step()
-        ld_host.copy_(logdet, non_blocking=True)
-        info_host.copy_(info, non_blocking=True)
+        for k, v in results.items():
+            back[k].copy_(v, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -354,8 +335,20 @@ def run_ours(args, rank, world, device_index):
     b.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a.elapsed_time(b) / e_reps
-    h2d = sum(pinned[k].numel() * 4 for k in ("Q", "B", "Xbar", "Sbar"))
-    d2h = count * 8 + count * 4
+    h2d = sum(pinned[k].numel() * pinned[k].element_size() for k in ("Q", "B", "Xbar", "Sbar"))
+    d2h = sum(v.numel() * v.element_size() for v in back.values())
+
+    # outputs of the instances the oracle samples (parity check of this very run)
+    sample_out = None
+    if rank == 0 and not args.no_cpu_baseline:
+        slot_of = {int(o): p for p, o in enumerate(order)}
+        sample_out = {}
+        for i in cpu_sample(count, args.cpu_sample):
+            p = slot_of[int(i)]
+            sample_out[int(i)] = dict(
+                L=lay.band_view(L, p).cpu().numpy(), S=lay.band_view(S, p).cpu().numpy(),
+                Qbar=lay.band_view(Qb, p).cpu().numpy(), X=lay.rhs_view(X, p).cpu().numpy(),
+                Bbar=lay.rhs_view(Bb, p).cpu().numpy(), logdet=float(logdet[p]), info=int(info[p]))
 
     entries = int(sum(n * (l + 1) for n, l in zip(lay.ns, lay.ls)))
     ms, ms_e2e, ms_fwd, ms_bwd = max_over_ranks([ms, ms_e2e, ms_fwd, ms_bwd], world, "cuda")
@@ -371,7 +364,7 @@ def run_ours(args, rank, world, device_index):
     return dict(lay=lay, plan=plan, ms=ms, ms_e2e=ms_e2e, ms_fwd=ms_fwd, ms_bwd=ms_bwd, entries=entries,
                 autotuned=autotuned,
                 fwd_bytes=fwd_b, bwd_bytes=bwd_b, floor_bytes=floor_b, clocks=clk, h2d=h2d, d2h=d2h,
-                fixups=fixups, plain=plain, launches=launches_per_step * args.steps)
+                fixups=fixups, plain=plain, launches=launches_per_step * args.steps, sample_out=sample_out)
 
 
 def run_plain(args, lay, host, torch, B, BT):
@@ -419,25 +412,54 @@ def run_plain(args, lay, host, torch, B, BT):
 
 # --------------------------------------------------------------------------- oracle arm
 
-def cpu_baseline(args, sample_count=None):
+# FP32 parity tolerances against the FP64 oracle (normwise per array per instance):
+# forward arrays and log-det 1e-4, gradients 1e-3.
+PARITY_TOL = {"L": 1e-4, "S": 1e-4, "X": 1e-4, "logdet": 1e-4, "Qbar": 1e-3, "Bbar": 1e-3}
+
+
+def cpu_baseline(args, sample_count=None, gpu_out=None):
+    """The FP64 C oracle on a bounded sample of the batch's own instances
+    (same shapes and seeds as the GPU run's rank 0, FP32-rounded inputs).
+    With `gpu_out` (sampled GPU outputs by original index) it also returns the
+    worst normwise error of every output against the oracle."""
     import oracle as O
     count = args.count
-    ns, ls = W.batched_shapes(count)
-    sample_count = sample_count or args.cpu_sample
-    rng = np.random.Generator(np.random.PCG64(11))
-    idx = np.sort(rng.choice(count, size=min(sample_count, count), replace=False))
-    insts = [W.make_instance(int(ns[i]), int(ls[i]), args.k, W.BASE_SEED + int(i)) for i in idx]
+    ls = tuple(int(x) for x in args.ls.split(","))
+    ns, lss = W.batched_shapes(count, seed=W.BASE_SEED, ls=ls)
+    idx = cpu_sample(count, sample_count or args.cpu_sample)
+    insts = [W.make_instance(int(ns[i]), int(lss[i]), args.k, W.BASE_SEED + int(i)) for i in idx]
     for ins in insts:                      # the CPU sees the same FP32-rounded inputs
-        ins.Q = ins.Q.astype(np.float32).astype(np.float64)
-        ins.B = ins.B.astype(np.float32).astype(np.float64)
+        for key in ("Q", "B", "Xbar", "Sbar"):
+            setattr(ins, key, getattr(ins, key).astype(np.float32).astype(np.float64))
     O.lib()
     t = time.perf_counter()
-    _, threads = O.batch_step(insts)
+    res, threads = O.batch_step(insts)
     dt = time.perf_counter() - t
     ent = sum(i.n * (i.l + 1) for i in insts)
-    return {"value": ent / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(insts)} of {count} instances ({ent} band entries), FP64 C oracle, "
-                      f"OpenMP over instances, {dt:.2f} s"}, dt
+    cb = {"value": ent / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+          "sample": f"{len(insts)} of {count} instances ({ent} band entries), FP64 C oracle, "
+                    f"OpenMP over instances, {dt:.2f} s"}
+    parity = None
+    if gpu_out is not None:
+        worst = {k: 0.0 for k in PARITY_TOL}
+        bad = 0
+        for i, r in zip(idx, res):
+            g = gpu_out[int(i)]
+            bad += int(g["info"] != 0 or r["info"] != 0)
+            for key in ("L", "S", "Qbar"):
+                worst[key] = max(worst[key], _normwise(g[key][: r[key].shape[0]], r[key]))
+            for key in ("X", "Bbar"):
+                worst[key] = max(worst[key], _normwise(g[key], r[key]))
+            worst["logdet"] = max(worst["logdet"], abs(g["logdet"] - r["logdet"]) / max(1.0, abs(r["logdet"])))
+        parity = {"instances": len(insts), "max_normwise_err": worst, "tol": PARITY_TOL, "non_spd": bad,
+                  "pass": bad == 0 and all(worst[k] <= PARITY_TOL[k] for k in worst)}
+    return cb, dt, parity
+
+
+def _normwise(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    den = np.max(np.abs(b)) if b.size else 0.0
+    return float(np.max(np.abs(a - b)) / den) if den > 0 else float(np.max(np.abs(a - b), initial=0.0))
 
 
 # --------------------------------------------------------------------------- the other configurations
@@ -583,7 +605,7 @@ def run_config(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=4096)
@@ -629,7 +651,7 @@ def main():
             cpu_baseline(args, sample_count=max(8, args.cpu_sample // 8))
         cb = None
         for _ in range(args.steps):
-            cb, dt = cpu_baseline(args, sample_count=max(8, args.cpu_sample // 8))
+            cb, dt, _ = cpu_baseline(args, sample_count=max(8, args.cpu_sample // 8))
             steps.append(dt)
         line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(steps), "higher_is_better": True,
@@ -659,9 +681,9 @@ def main():
         dom, dom_ms, dom_bytes = "banded_gmm_forward", r["ms_fwd"], r["fwd_bytes"]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     step_gbs = (r["fwd_bytes"] + r["bwd_bytes"]) / (r["ms"] * 1e-3) / 1e9
-    cb = None
+    cb = parity = None
     if not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(args)
+        cb, _, parity = cpu_baseline(args, gpu_out=r["sample_out"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
@@ -688,6 +710,7 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "cpu_baseline": cb,
+        "parity": parity,
     }
     if r["autotuned"] is not None:
         line["config"]["autotuned"] = r["autotuned"]

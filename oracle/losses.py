@@ -184,3 +184,123 @@ def matern_kl(t, ell, s2, Lq, m):
     quad = float(v @ v)
     logs = 2.0 * float(np.sum(np.log(Lq[0]))) - 2.0 * float(np.sum(np.log(np.abs(M[0]))))
     return 0.5 * (tr + logs + quad - N)
+
+
+# ---------------------------------------------------------------------------
+# Reverse mode of the Matern KL (Eq. 5 / Alg. 7 with Q_p = M^T M), composed
+# from the oracle's operator adjoints (Table 1 for the product and the
+# band-vector product, Alg. 4 for the subset inverse) and the derivative of
+# M with respect to the lengthscale taken analytically from the closed forms
+# above.
+# ---------------------------------------------------------------------------
+
+def matern_M_band_dell(t, ell, s2):
+    """(M, dM/d ell) in (lo, up) = (3, 0) band storage.
+
+    With lam = sqrt(3)/ell, x = lam D, e = exp(-x), q = e^2 (D a gap):
+      dA/dlam = e [[-D x, -D^2], [lam D (x - 2), -D (2 - x)]]
+      dSigma_00/dlam = 4 s2 x^2 q D
+      dSigma_01/dlam = 2 s2 x^2 q (3 - 2x)
+      dSigma_11/dlam = s2 (2 lam f(x) + 4 lam x (1 - x)^2 q),
+        f(x) = 1 - q (1 - 2x + 2x^2)  (the Sigma_11 bracket)
+    (from f'(x) = 4 x^2 e^{-2x} and 4 (1 - x)^2 e^{-2x} for the two brackets),
+    then the chain rule through the 2x2 Cholesky factor, its inverse and
+    -C^{-1} A, and d lam / d ell = -lam / ell."""
+    lam = math.sqrt(3.0) / ell
+    t = np.asarray(t, dtype=np.float64)
+    n = t.shape[0]
+    D = np.diff(t)
+    A, Sig, Pinf = matern_transition(D, ell, s2)
+    x = lam * D
+    e = np.exp(-x)
+    q = e * e
+    dA = np.empty(D.shape + (2, 2))
+    dA[..., 0, 0] = -e * D * x
+    dA[..., 0, 1] = -e * D * D
+    dA[..., 1, 0] = e * lam * D * (x - 2.0)
+    dA[..., 1, 1] = -e * D * (2.0 - x)
+    dS00 = 4.0 * s2 * x * x * q * D
+    dS01 = 2.0 * s2 * x * x * q * (3.0 - 2.0 * x)
+    dS11 = s2 * (2.0 * lam * one_minus_exp_poly(x, -2.0) + 4.0 * lam * x * (1.0 - x) ** 2 * q)
+    # Cholesky factors of Sigma and their derivatives
+    c00 = np.sqrt(Sig[..., 0, 0])
+    c10 = Sig[..., 1, 0] / c00
+    c11 = np.sqrt(Sig[..., 1, 1] - c10 * c10)
+    dc00 = dS00 / (2.0 * c00)
+    dc10 = (dS01 - c10 * dc00) / c00
+    dc11 = (dS11 - 2.0 * c10 * dc10) / (2.0 * c11)
+    # the first block uses chol(Pinf) = diag(sqrt(s2), lam sqrt(s2))
+    rs = math.sqrt(s2)
+    C00 = np.concatenate([[rs], c00])
+    C10 = np.concatenate([[0.0], c10])
+    C11 = np.concatenate([[lam * rs], c11])
+    dC00 = np.concatenate([[0.0], dc00])
+    dC10 = np.concatenate([[0.0], dc10])
+    dC11 = np.concatenate([[rs], dc11])
+    # inverse of the lower 2x2 factor [[c00, 0], [c10, c11]] and its derivative
+    I00, I11 = 1.0 / C00, 1.0 / C11
+    I10 = -C10 / (C00 * C11)
+    dI00, dI11 = -dC00 / (C00 * C00), -dC11 / (C11 * C11)
+    dI10 = -(dC10 * C00 * C11 - C10 * (dC00 * C11 + C00 * dC11)) / (C00 * C11) ** 2
+    Ci = np.zeros((n, 2, 2))
+    dCi = np.zeros((n, 2, 2))
+    Ci[:, 0, 0], Ci[:, 1, 0], Ci[:, 1, 1] = I00, I10, I11
+    dCi[:, 0, 0], dCi[:, 1, 0], dCi[:, 1, 1] = dI00, dI10, dI11
+    Off = -(Ci[1:] @ A)
+    dOff = -(dCi[1:] @ A + Ci[1:] @ dA)
+
+    def band_of(Cd, Od):
+        M = np.zeros((4, 2 * n))
+        M[0, 0::2] = Cd[:, 0, 0]
+        M[0, 1::2] = Cd[:, 1, 1]
+        M[1, 0::2] = Cd[:, 1, 0]
+        k = np.arange(1, n)
+        for a in range(2):
+            for c in range(2):
+                M[2 + a - c, 2 * k - 2 + c] = Od[:, a, c]
+        return M
+    M = band_of(Ci, Off)
+    dM_dlam = band_of(dCi, dOff)
+    return M, dM_dlam * (-lam / ell)
+
+
+def matern_kl_grad(t, ell, s2, Lq, m):
+    """KL of matern_kl and its gradients (KL, Lq_bar, m_bar, ell_bar).
+
+    KL = 1/2 [tr(Q_p S_q) + |M m|^2 - N + 2 sum log Lq_ii - 2 sum log|M_ii|],
+    Q_p = band_3(M^T M), S_q = band_3((Lq Lq^T)^{-1}):
+      S_q bar  = 1/2 w Q_p   (w: 1 on the diagonal, 2 off it: trace over lower storage)
+      Lq bar   = Alg. 4 adjoint of S_q with S_q bar, plus 1/Lq_ii on the diagonal
+      Q_p bar  = 1/2 w S_q;  M bar from the product adjoint of M^T M (Table 1)
+      v = M m:  m bar = M^T v, M bar += band_3(v m^T)  (band-vector adjoint, Table 1)
+      M bar_ii -= 1/M_ii;    ell bar = sum M bar * dM/d ell."""
+    from . import band_matvec, band_matvec_vjp, product_vjp
+    M, dM = matern_M_band_dell(t, ell, s2)
+    Lq = np.asarray(Lq, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    N = Lq.shape[1]
+    w = sym_weights(4)
+    Qp = product(M, 3, 0, 1, M, 3, 0, 0, 3, 0)
+    Sq = subset_inverse(Lq)
+    v = band_matvec(M, 3, 0, 0, m[None])[0]
+    kl = 0.5 * (trace_sym(Sq, Qp) + float(v @ v) - N + 2.0 * float(np.sum(np.log(Lq[0])))
+                - 2.0 * float(np.sum(np.log(np.abs(M[0])))))
+    Lq_bar = subset_inverse_vjp(Lq, Sq, _zero_corners(0.5 * w * Qp))
+    Lq_bar[0] += 1.0 / Lq[0]
+    Qp_bar = _zero_corners(0.5 * w * Sq)
+    Ma, Mb = product_vjp(M, 3, 0, 1, M, 3, 0, 0, Qp_bar, 3, 0)
+    M_bar = Ma + Mb
+    Mv_bar, m_bar = band_matvec_vjp(M, 3, 0, 0, m[None], v[None])
+    M_bar = M_bar + Mv_bar
+    M_bar[0] -= 1.0 / M[0]
+    ell_bar = float(np.sum(_zero_corners(M_bar) * _zero_corners(dM)))
+    return kl, _zero_corners(Lq_bar), m_bar[0], ell_bar
+
+
+def _zero_corners(band):
+    """Zero the undefined corners band[d, j], j + d >= n, of a lower band."""
+    band = np.array(band, dtype=np.float64)
+    n = band.shape[1]
+    for d in range(1, band.shape[0]):
+        band[d, max(n - d, 0):] = 0.0
+    return band

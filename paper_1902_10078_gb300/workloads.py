@@ -198,3 +198,48 @@ def lower_band_from_dense(M: np.ndarray, l: int) -> np.ndarray:
         j = np.arange(0, n - d)
         band[d, : n - d] = M[j + d, j]
     return band
+
+
+# ---------------------------------------------------------------------------
+# Batch inputs in a pool layout (host side, parallel over instances)
+# ---------------------------------------------------------------------------
+
+def _fill_worker(args):
+    """Draw the instances of one chunk: (slot, seed, n, l) -> FP32 band / RHS arrays."""
+    jobs, k = args
+    out = []
+    for slot, seed, n, l in jobs:
+        ins = make_instance(n, l, k, seed)
+        out.append((slot, ins.Q.astype(np.float32), ins.Sbar.astype(np.float32), ins.B.astype(np.float32),
+                    ins.Xbar.astype(np.float32)))
+    return out
+
+
+def fill_pools(lay, seeds, workers=1):
+    """FP32 host pools Q, Sbar (band) and B, Xbar (RHS) of a batch in the
+    arrangement of ``lay`` (a batch.Layout); instance ``slot`` of the layout
+    draws ``make_instance(lay.ns[slot], lay.ls[slot], lay.k, seeds[slot])``, so
+    a reordered layout keeps each instance's data by passing its seed along.
+    ``workers`` > 1 uses a spawn pool (safe before or after CUDA use)."""
+    import multiprocessing as mp
+    pools = {"Q": np.zeros(lay.band_elems, np.float32), "Sbar": np.zeros(lay.band_elems, np.float32),
+             "B": np.zeros(lay.rhs_elems, np.float32), "Xbar": np.zeros(lay.rhs_elems, np.float32)}
+    items = [(s, int(seeds[s]), int(lay.ns[s]), int(lay.ls[s])) for s in range(lay.count)]
+    chunks = max(1, min(workers * 4, lay.count))
+    bounds = np.linspace(0, lay.count, chunks + 1).astype(int)
+    jobs = [(items[bounds[c]:bounds[c + 1]], lay.k) for c in range(chunks) if bounds[c + 1] > bounds[c]]
+
+    def put(res):
+        for s, q, sb, b, xb in res:
+            lay.band_view(pools["Q"], s)[: q.shape[0]] = q
+            lay.band_view(pools["Sbar"], s)[: sb.shape[0]] = sb
+            lay.rhs_view(pools["B"], s)[: b.shape[0]] = b
+            lay.rhs_view(pools["Xbar"], s)[: xb.shape[0]] = xb
+    if workers > 1:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for res in pool.imap_unordered(_fill_worker, jobs):
+                put(res)
+    else:
+        for j in jobs:
+            put(_fill_worker(j))
+    return pools

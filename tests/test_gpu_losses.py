@@ -7,10 +7,11 @@ reverse mode through the torch.autograd.Function adjoints.
   matches central finite differences of the GPU loss on 50 random stored
   entries.
 * Matern-3/2 state-space KL: sum over processes of KL(N(m, (Lq Lq^T)^{-1}) ||
-  N(0, Q_p^{-1})) with Q_p = M^T M built from (t, lengthscale).  Value against
-  the oracle; gradients in the lengthscales, Lq and m against central finite
-  differences of the oracle's KL.  The full-size batch (256 processes,
-  N = 100000 states each) checks the value.
+  N(0, Q_p^{-1})) with Q_p = M^T M built from (t, lengthscale), on the
+  workload's own Exp(1) gaps.  Value against the oracle; gradients in the
+  lengthscales, Lq and m element by element against the oracle's composed
+  KL adjoint, on a small batch and on a slice of the full-size batch (256
+  processes, N = 100000 states each).
 """
 import numpy as np
 import pytest
@@ -108,53 +109,42 @@ def oracle_kl(procs, dtype, ells=None, Lqs=None, ms=None):
     return tot
 
 
+def check_kl_gradients(procs, dtype, lay, Lq, m, ells, idx, tol):
+    """GPU gradients of the processes in `idx` against the oracle's composed KL
+    adjoint (normwise per array per process; the lengthscale gradient relative
+    to max(1, |ref|))."""
+    gL = lay.unpack_band(Lq.grad)
+    gm = lay.unpack_rhs(m.grad)
+    ge = ells.grad.detach().cpu().numpy()
+    worst = dict(Lq=0.0, m=0.0, ell=0.0)
+    for i in idx:
+        p = procs[i]
+        _, rL, rm, re = OL.matern_kl_grad(p.t, p.lengthscale, p.variance, rounded(p.Lq, dtype),
+                                          rounded(p.m, dtype))
+        worst["Lq"] = max(worst["Lq"], relerr(gL[i], rL))
+        worst["m"] = max(worst["m"], relerr(gm[i][0], rm))
+        worst["ell"] = max(worst["ell"], abs(float(ge[i]) - re) / max(1.0, abs(re)))
+    for key, v in worst.items():
+        assert v <= tol, f"{key} gradient: error {v:.3e} > {tol:.1e}"
+    return worst
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
 @pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
 def test_matern_kl_value_and_gradients(dtype):
-    # gaps of at least 0.5 keep Q_p moderate, so that central differences of one
-    # process's KL resolve single-entry gradients (the full-size test keeps the
-    # workload's own gaps)
+    # the workload's own gaps (Exp(1), no floor): Q_p reaches ~1e15 at the smallest ones
     count, n = 6, 1500
-    procs, lay, plan, Lq, m, ells, ctx = matern_setup(count, n, dtype, min_gap=0.5)
+    procs, lay, plan, Lq, m, ells, ctx = matern_setup(count, n, dtype)
     assert B.bnd_plan_layout(plan.handle) == B.LAYOUT_PANELS
     kl = gpu_kl(plan, ctx, ells, Lq, m)
     kl.backward()
     ref = oracle_kl(procs, dtype)
-    tol_v, tol_g = (1e-10, 1e-6) if dtype == B.BND_F64 else (1e-4, 2e-3)
+    tol_v, tol_g = (1e-10, 1e-10) if dtype == B.BND_F64 else (1e-4, 1e-3)
     assert abs(float(kl.detach()) - ref) <= tol_v * max(1.0, abs(ref)), (float(kl.detach()), ref)
-    Lqs = [rounded(p.Lq, dtype) for p in procs]
-    ms = [rounded(p.m, dtype) for p in procs]
-
-    def kl_i(i, ell=None, Lq_i=None, m_i=None):
-        p = procs[i]
-        return OL.matern_kl(p.t, p.lengthscale if ell is None else ell, p.variance,
-                            Lqs[i] if Lq_i is None else Lq_i, ms[i] if m_i is None else m_i)
-
-    # lengthscale gradients vs central differences of the oracle KL of that process
-    for i in range(count):
-        e0 = procs[i].lengthscale
-        h = 1e-5 * e0
-        fd = (kl_i(i, ell=e0 + h) - kl_i(i, ell=e0 - h)) / (2 * h)
-        g = float(ells.grad[i])
-        assert abs(g - fd) <= tol_g * max(1.0, abs(fd)), (i, g, fd)
-    # Lq and m gradients on a few entries
-    rng = W.rng_for(77)
-    gL = lay.unpack_band(Lq.grad)
-    gm = lay.unpack_rhs(m.grad)
-    h = 1e-5
-    for _ in range(8):
-        i = int(rng.integers(0, count))
-        d, j = int(rng.integers(0, 4)), int(rng.integers(0, 2 * n - 3))
-        Lp, Lm = Lqs[i].copy(), Lqs[i].copy()
-        Lp[d, j] += h
-        Lm[d, j] -= h
-        fd = (kl_i(i, Lq_i=Lp) - kl_i(i, Lq_i=Lm)) / (2 * h)
-        assert abs(gL[i][d, j] - fd) <= tol_g * max(1.0, abs(fd)), (i, d, j, gL[i][d, j], fd)
-        j = int(rng.integers(0, 2 * n))
-        mp, mm = ms[i].copy(), ms[i].copy()
-        mp[j] += h
-        mm[j] -= h
-        fd = (kl_i(i, m_i=mp) - kl_i(i, m_i=mm)) / (2 * h)
-        assert abs(gm[i][0, j] - fd) <= tol_g * max(1.0, abs(fd)), (i, j, gm[i][0, j], fd)
+    check_kl_gradients(procs, dtype, lay, Lq, m, ells, range(count), tol_g)
 
 
 @pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
@@ -164,6 +154,7 @@ def test_matern_kl_full_size(dtype):
     kl = gpu_kl(plan, ctx, ells, Lq, m)
     kl.backward()
     ref = oracle_kl(procs, dtype)
-    tol = 1e-10 if dtype == B.BND_F64 else 1e-4
+    tol, tol_g = (1e-10, 1e-10) if dtype == B.BND_F64 else (1e-4, 1e-3)
     assert abs(float(kl.detach()) - ref) <= tol * max(1.0, abs(ref)), (float(kl.detach()), ref)
-    assert torch.isfinite(ells.grad).all() and torch.isfinite(Lq.grad).all() and torch.isfinite(m.grad).all()
+    # gradients of a slice of the batch (first, middle, last panel groups) against the oracle adjoint
+    check_kl_gradients(procs, dtype, lay, Lq, m, ells, [0, 31, 32, 128, 255], tol_g)

@@ -199,3 +199,47 @@ def test_wide_bands_warp_kernel(dtype, arr):
         assert_close("Qbar", Qg[c], r["Qbar"], tol["grad"])
         assert_close("Bbar", Bg[c], r["Bbar"], tol["grad"])
         assert abs(got["logdet"][c] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))
+
+
+def run_separate(lay, plan, insts):
+    """Forward + backward through the separate operators (any number of RHS):
+    C, (L L^T)^{-1} B, I; then the solve, subset-inverse and Cholesky adjoints
+    accumulated into one L-bar (Table 1, Alg. 4, Alg. 2 with the log-det term)."""
+    Q = dev(lay, lay.pack_band([i.Q for i in insts]))
+    Bp = dev(lay, lay.pack_rhs([i.B for i in insts]))
+    Xb = dev(lay, lay.pack_rhs([i.Xbar for i in insts]))
+    Sb = dev(lay, lay.pack_band([i.Sbar for i in insts]))
+    L, S, Lb, Qb = (lay.band_pool() for _ in range(4))
+    X, Bb = lay.rhs_pool(), lay.rhs_pool()
+    logdet = torch.empty(lay.count, dtype=torch.float64, device="cuda")
+    info = torch.empty(lay.count, dtype=torch.int32, device="cuda")
+    ldb = torch.full((lay.count,), 0.5, dtype=torch.float64, device="cuda")
+    B.banded_cholesky(plan.handle, Q, L, logdet, info)
+    B.banded_solve(plan.handle, L, Bp, X, 2)
+    B.banded_subset_inverse(plan.handle, L, S)
+    B.banded_solve_vjp(plan.handle, L, X, Xb, 2, Bb, Lb, 0)
+    B.banded_subset_inverse_vjp(plan.handle, L, S, Sb, Lb, 1)
+    B.banded_cholesky_vjp(plan.handle, L, Lb, ldb, Qb, 0)
+    sync()
+    return dict(L=L, S=S, X=X, Qb=Qb, Bb=Bb, logdet=logdet.cpu().numpy(), info=info.cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_wide_bands_sixteen_rhs(dtype):
+    """The wide-band workload's shape at a few thousand rows: l = 64 and 128 with
+    16 right-hand sides (four RHS blocks per solve), against the oracle."""
+    shapes = [(2500, 64), (2000, 128)]
+    insts, lay, plan = setup(shapes, 16, dtype, dict(seg_len=-1))
+    got = run_separate(lay, plan, insts)
+    res, _ = O.batch_step(insts)
+    tol = TOL[dtype]
+    Lg, Sg, Qg = lay.unpack_band(got["L"]), lay.unpack_band(got["S"]), lay.unpack_band(got["Qb"])
+    Xg, Bg = lay.unpack_rhs(got["X"]), lay.unpack_rhs(got["Bb"])
+    for c, r in enumerate(res):
+        assert got["info"][c] == 0
+        assert_close("L", Lg[c], r["L"], tol["fwd"])
+        assert_close("S", Sg[c], r["S"], tol["fwd"])
+        assert_close("X", Xg[c], r["X"], tol["fwd"])
+        assert_close("Qbar", Qg[c], r["Qbar"], tol["grad"])
+        assert_close("Bbar", Bg[c], r["Bbar"], tol["grad"])
+        assert abs(got["logdet"][c] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))

@@ -553,3 +553,112 @@ def test_matern_kl_at_tiny_gaps_matches_high_precision(oracle):
     quad = (mv.T * Qp * mv)[0]
     ref = 0.5 * (tr + quad - N + mpmath.log(mpmath.det(Qq)) - mpmath.log(mpmath.det(Qp)))
     assert abs(kl - float(ref)) <= 1e-9 * abs(float(ref)), (kl, float(ref))
+
+
+def _matern_kernel_cov_torch(t, ell, s2):
+    """The joint (f, f') covariance of matern_dense_cov, as a torch function of ell
+    (autograd pins the lengthscale gradient through the kernel, not the SDE)."""
+    lam = math.sqrt(3.0) / ell
+    tt = torch.tensor(t, dtype=torch.float64)
+    tau = tt[:, None] - tt[None, :]
+    a = tau.abs()
+    e = torch.exp(-lam * a)
+    n = t.shape[0]
+    K = torch.zeros((2 * n, 2 * n), dtype=torch.float64)
+    K[0::2, 0::2] = s2 * (1 + lam * a) * e
+    K[0::2, 1::2] = s2 * lam * lam * tau * e
+    K[1::2, 0::2] = -s2 * lam * lam * tau * e
+    K[1::2, 1::2] = s2 * lam * lam * (1 - lam * a) * e
+    return K
+
+
+def test_matern_kl_grad_matches_dense_autograd(oracle):
+    """The composed KL adjoint (product, band-vector and Alg. 4 adjoints, dM/d ell in
+    closed form) against torch autograd of the dense Gaussian KL whose prior
+    precision is the inverse of the kernel covariance."""
+    from oracle.losses import matern_kl_grad
+    rng = W.rng_for(93)
+    n = 10
+    t = np.concatenate([[0.0], np.cumsum(rng.exponential(1.0, n - 1) + 0.05)])
+    ell0, s2 = 1.7, 1.0
+    N = 2 * n
+    Lq = np.zeros((4, N))
+    Lq[0] = 1.0 + 0.1 * rng.uniform(size=N)
+    Lq[1:] = rng.normal(0.0, 0.05, (3, N))
+    W.zero_corners(Lq)
+    m = rng.normal(0.0, 0.1, N)
+    kl, gL, gm, ge = matern_kl_grad(t, ell0, s2, Lq, m)
+    ell = torch.tensor(ell0, dtype=torch.float64, requires_grad=True)
+    x = torch.tensor(Lq, requires_grad=True)
+    mt = torch.tensor(m, requires_grad=True)
+    K = _matern_kernel_cov_torch(t, ell, s2)
+    Qp = torch.linalg.inv(K)
+    Lt = low_from_stored(x, N, 3)
+    Sq = torch.linalg.inv(Lt @ Lt.T)
+    ref = 0.5 * (torch.trace(Qp @ Sq) + mt @ Qp @ mt - N + torch.logdet(Lt @ Lt.T) + torch.logdet(K))
+    ref.backward()
+    assert abs(kl - float(ref.detach())) < 1e-10 * abs(float(ref.detach()))
+    assert abs(ge - float(ell.grad)) < 1e-8 * abs(float(ell.grad)), (ge, float(ell.grad))
+    assert rel(gL, W.zero_corners(x.grad.numpy().copy())) < 1e-9
+    assert rel(gm, mt.grad.numpy()) < 1e-9
+
+
+def test_matern_kl_grad_at_tiny_gaps_matches_high_precision(oracle):
+    """Gaps of 1e-6 and 2e-4 (the workload's smallest are of that order): the
+    lengthscale gradient against a 60-digit central difference of the dense KL,
+    and the m and Lq gradients against the 60-digit dense gradient formulas
+    (m bar = Q_p m; Lq bar = -(Q_q^{-1} Q_p Q_q^{-1}) Lq + Lq^{-T} restricted to the band)."""
+    import mpmath
+    from oracle.losses import matern_kl_grad
+    mpmath.mp.dps = 60
+    rng = W.rng_for(97)
+    n = 6
+    gaps = np.array([0.7, 1e-6, 1.3, 0.2, 2e-4])
+    t = np.concatenate([[0.0], np.cumsum(gaps)])
+    ell0, s2 = 1.1, 1.0
+    N = 2 * n
+    Lq = np.zeros((4, N))
+    Lq[0] = 1.0 + 0.1 * rng.uniform(size=N)
+    Lq[1:] = rng.normal(0.0, 0.05, (3, N))
+    W.zero_corners(Lq)
+    m = rng.normal(0.0, 0.1, N)
+    kl, gL, gm, ge = matern_kl_grad(t, ell0, s2, Lq, m)
+
+    def prior_precision(ell):
+        lam = mpmath.sqrt(3) / ell
+        K = mpmath.matrix(N, N)
+        for a in range(n):
+            for b in range(n):
+                tau = mpmath.mpf(float(t[a])) - mpmath.mpf(float(t[b]))
+                e = mpmath.exp(-lam * abs(tau))
+                K[2 * a, 2 * b] = s2 * (1 + lam * abs(tau)) * e
+                K[2 * a, 2 * b + 1] = s2 * lam * lam * tau * e
+                K[2 * a + 1, 2 * b] = -s2 * lam * lam * tau * e
+                K[2 * a + 1, 2 * b + 1] = s2 * lam * lam * (1 - lam * abs(tau)) * e
+        return mpmath.inverse(K)
+
+    Ld = mpmath.matrix(N, N)
+    for d in range(4):
+        for j in range(N - d):
+            Ld[j + d, j] = mpmath.mpf(float(Lq[d, j]))
+    Sq = mpmath.inverse(Ld * Ld.T)
+    mv = mpmath.matrix([mpmath.mpf(float(v)) for v in m])
+
+    def kl_of(ell):
+        Qp = prior_precision(ell)
+        tr = sum(Qp[i, j] * Sq[j, i] for i in range(N) for j in range(N))
+        return 0.5 * (tr + (mv.T * Qp * mv)[0] - N + mpmath.log(mpmath.det(Ld * Ld.T)) - mpmath.log(mpmath.det(Qp)))
+
+    e0 = mpmath.mpf(ell0)
+    h = mpmath.mpf("1e-25")
+    ref_ge = float((kl_of(e0 + h) - kl_of(e0 - h)) / (2 * h))
+    assert abs(ge - ref_ge) <= 1e-8 * abs(ref_ge), (ge, ref_ge)
+    Qp = prior_precision(e0)
+    ref_gm = np.array([float(v) for v in (Qp * mv)])
+    assert rel(gm, ref_gm) < 1e-9
+    G = -(Sq * Qp * Sq) * Ld + mpmath.inverse(Ld).T     # d KL / d L (dense), lower part is the stored gradient
+    ref_gL = np.zeros_like(Lq)
+    for d in range(4):
+        for j in range(N - d):
+            ref_gL[d, j] = float(G[j + d, j])
+    assert rel(gL, ref_gL) < 1e-9
