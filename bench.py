@@ -231,7 +231,8 @@ def run_ours(args, rank, world, device_index):
     info = torch.empty(count, dtype=torch.int32, device="cuda")
     ldbar = torch.full((count,), 0.5, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    tuning = dict(seg_len=args.seg_len, warmup=args.warm, flags=args.flags)
+    tuning = dict(seg_len=args.seg_len, warmup=args.warm, flags=args.flags, warm_per_l=args.warm_per_l,
+                  warm_base=args.warm_base)
     autotuned = None
     if args.autotune:
         def make_step(pl):
@@ -464,6 +465,18 @@ def _normwise(a, b):
 
 # --------------------------------------------------------------------------- the other configurations
 
+PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks_gb300.json")
+
+
+def compute_peaks():
+    """FP32 / FP64 FMA throughput measured by microbench/peaks.cu (committed summary)."""
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def run_config(args):
     """Supplementary measurements of the other workload configurations (one
     JSON line each; the headline line is the uneven batch).  Every number is
@@ -510,15 +523,30 @@ def run_config(args):
 
     lines = []
     dts = {"f64": B.BND_F64, "f32": B.BND_F32}
+    peaks = compute_peaks()
     if args.config == 0:
-        lay, plan, step, info = gmm_setup([(1000, 2)], 1, B.BND_F64, dict(seg_len=-1))
-        ms = timed(step, 200)
-        lines.append({"config": "plain single instance n=1000, l=2, 1 RHS, FP64: fused Cholesky + solve + "
-                      "log-det + subset inverse, forward and backward", "us_per_step": 1e3 * ms,
-                      "bound": "launch latency and the sequential chain (one lane)"})
+        import oracle as O
+        for name, dt in dts.items():
+            lay, plan, step, info = gmm_setup([(1000, 2)], 1, dt)
+            ms = timed(step, 200)
+            ins = W.make_instance(1000, 2, 1, W.BASE_SEED)
+            O.lib()
+            reps, t0 = 200, time.perf_counter()
+            for _ in range(reps):
+                O.batch_step([ins])
+            cpu_us = 1e6 * (time.perf_counter() - t0) / reps
+            lines.append({"config": f"plain single instance n=1000, l=2, 1 RHS, {name}: fused Cholesky + solve + "
+                          "log-det + subset inverse, forward and backward", "us_per_step": 1e3 * ms,
+                          "segments": plan.chains, "oracle_us_per_step_1core": cpu_us,
+                          "bound": "the per-row dependent chain of each segment (FP64: ~650-cycle sqrt and "
+                                   "division, 64-cycle FMA on this part)"})
     elif args.config == 1:
+        from oracle import losses as OL
         n, l = 100_000, 3
         Q, b, Wt = W.long_chain_config(n, l)
+        t0 = time.perf_counter()
+        OL.chain_loss(Q, b, Wt)
+        cpu_ms = 1e3 * (time.perf_counter() - t0)
         for name, dt in dts.items():
             lay = BT.Layout([n], [l], 1, dt)
             plan = BT.Plan(lay)
@@ -533,46 +561,30 @@ def run_config(args):
                 loss.backward()
             ms = timed(step, 20)
             lines.append({"config": f"long chain n={n}, l={l}, loss forward + backward through autograd, {name}",
-                          "ms_per_step": ms, "ns_per_row": 1e6 * ms / n, "segments": plan.chains})
+                          "ms_per_step": ms, "ns_per_row": 1e6 * ms / n, "segments": plan.chains,
+                          "oracle_ms_per_step_1core": cpu_ms})
     elif args.config == 3:
-        # the fused step carries at most 4 RHS; 16 RHS run through the separate operators:
-        # forward C, S (Q^{-1} B, chunks of 4 columns), I; backward solve, subset-inverse and
-        # Cholesky adjoints (accumulating into one L-bar)
+        # fused forward + backward with all 16 right-hand sides in each sweep (wide-band block kernels)
         for l in args.wide_ls:
-            n, k = 200_000, 16
-            ins = W.make_instance(n, l, k, W.BASE_SEED)
-            lay = BT.Layout([n], [l], k, B.BND_F64)
-            plan = BT.Plan(lay, dict(seg_len=-1))
-            Q = torch.from_numpy(lay.pack_band([ins.Q])).cuda()
-            Bm = torch.from_numpy(lay.pack_rhs([ins.B])).cuda()
-            Xb = torch.from_numpy(lay.pack_rhs([ins.Xbar])).cuda()
-            Sb = torch.from_numpy(lay.pack_band([ins.Sbar])).cuda()
-            L, S, Lb, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool(), lay.band_pool()
-            X, Bb = lay.rhs_pool(), lay.rhs_pool()
-            ld = torch.empty(1, dtype=torch.float64, device="cuda")
-            info = torch.empty(1, dtype=torch.int32, device="cuda")
-            ldb = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
-
-            def step():
-                B.banded_cholesky(plan.handle, Q, L, ld, info)
-                B.banded_solve(plan.handle, L, Bm, X, 2)
-                B.banded_subset_inverse(plan.handle, L, S)
-                B.banded_solve_vjp(plan.handle, L, X, Xb, 2, Bb, Lb, 0)
-                B.banded_subset_inverse_vjp(plan.handle, L, S, Sb, Lb, 1)
-                B.banded_cholesky_vjp(plan.handle, L, Lb, ldb, Qb, 0)
-            step()                                  # one warm-up call: this path runs for seconds
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b)
-            flops = 9.0 * n * l * l
-            lines.append({"config": f"wide band n={n}, l={l}, k={k}, FP64: Cholesky, Q^-1 B, subset inverse "
-                          "and their adjoints", "ms_per_step": ms, "gflops_per_s": flops / (ms * 1e-3) / 1e9,
-                          "info": int(info.item()),
-                          "path": "generic kernels: one lane per instance, windows in memory"})
+            for name in args.wide_dtypes:
+                dt = dts[name]
+                n, k = 200_000, 16
+                lay, plan, step, info = gmm_setup([(n, l)], k, dt)
+                step()
+                torch.cuda.synchronize()
+                ms = timed(step, 3)
+                flops = 9.0 * n * l * l
+                pk = peaks.get("fp64_fma_tflops" if name == "f64" else "fp32_fma_tflops")
+                gf = flops / (ms * 1e-3) / 1e9
+                lines.append({"config": f"wide band n={n}, l={l}, k={k}, {name}: Cholesky, Q^-1 B, subset inverse "
+                              "and their adjoints (fused forward + backward)", "ms_per_step": ms,
+                              "gflops_per_s": gf, "flops_per_step": flops, "info": int(info[0].item()),
+                              "roofline": {"bound": "fp64" if name == "f64" else "fp32", "achieved_tflops": gf / 1e3,
+                                           "peak_tflops": pk, "frac": (gf / 1e3) / pk if pk else None,
+                                           "peak_source": "measured (microbench/peaks.cu)"},
+                              "path": "one thread block per chain, computed window in shared memory, "
+                                      "O(l^2) row work spread over 512 threads; segments "
+                                      f"{plan.chains}"})
     elif args.config == 4:
         count, n = 256, 50_000
         procs = W.matern_batch(count, n)
@@ -590,12 +602,19 @@ def run_config(args):
                 Lq.grad = m.grad = ells.grad = None
                 kl = LS.matern_kl(plan, prior, ells, Lq, m, wsym, dmask)
                 kl.backward()
+
+            def prior_only():
+                e = ells.detach().requires_grad_(True)
+                Mp = prior.band(e)
+                Mp.sum().backward()
             ms = timed(step, 5)
+            ms_prior = timed(prior_only, 5)
             lines.append({"config": f"Matern-3/2 KL, {count} processes x {2 * n} states, l=3, forward + backward "
                           f"in L_q, m and the lengthscales, {name}", "ms_per_step": ms,
+                          "ms_prior_construction_fwd_bwd": ms_prior,
                           "band_entries_per_s": count * 2 * n * 4 / (ms * 1e-3),
                           "note": "includes the FP64 torch construction of the prior factor M (flat over all "
-                                  "processes) and its backward"})
+                                  "processes) and its backward, timed alone in ms_prior_construction_fwd_bwd"})
     for line in lines:
         print(json.dumps(line), flush=True)
 
@@ -613,6 +632,8 @@ def main():
     ap.add_argument("--seg-len", type=int, default=0, help="rows per segment (0: the library default)")
     ap.add_argument("--warm", type=int, default=0, help="warm-up rows (0: per-bandwidth default)")
     ap.add_argument("--flags", type=int, default=0, help="plan tuning flags (see bnd_tuning)")
+    ap.add_argument("--warm-per-l", type=int, default=0, help="warm-up rows per unit of bandwidth (0: default)")
+    ap.add_argument("--warm-base", type=int, default=0, help="warm-up rows added to warm_per_l * l")
     ap.add_argument("--ls", default="1,2,3,5,7", help="bandwidths drawn uniformly (profiling cases)")
     ap.add_argument("--layout", default="panels", choices=["panels", "rows"],
                     help="pool arrangement: 32-instance panels (cs = 32) or one contiguous row per diagonal")
@@ -625,7 +646,8 @@ def main():
                     help="choose the segment length by timing candidates on this batch first")
     ap.add_argument("--config", type=int, default=None, choices=[0, 1, 3, 4],
                     help="time another workload configuration instead of the uneven batch")
-    ap.add_argument("--wide-ls", type=int, nargs="+", default=[64], help="bandwidths of --config 3")
+    ap.add_argument("--wide-ls", type=int, nargs="+", default=[64, 128], help="bandwidths of --config 3")
+    ap.add_argument("--wide-dtypes", nargs="+", default=["f32", "f64"], help="dtypes of --config 3")
     ap.add_argument("--profile-once", action="store_true",
                     help="run one forward and one backward call in NVTX ranges (for ncu) and exit")
     ap.add_argument("--summarize-ncu", default=None, help="ncu --csv file of one backward call -> profiles/")
@@ -690,7 +712,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "layout": LAYOUT_NOTE[args.layout],
                    "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
-                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len or ("library default: 384" if args.layout == "panels" else "library default: 2048"), "warmup_rows": args.warm or "24 l + 32",
+                   "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len or ("library default: 384" if args.layout == "panels" else "library default: 2048"), "warmup_rows": args.warm or (f"{args.warm_per_l} l + {args.warm_base}" if args.warm_per_l else "library default"),
                    "chains": r["plan"].chains, "warp_tasks": r["plan"].tasks, "graph": True,
                    "l2": "inputs (~%.1f GB) exceed L2; no flush" % (r["h2d"] / 1e9),
                    "parallelism": f"instances sharded per GPU (weak), dp{world}", "segment_fixups": r["fixups"]},

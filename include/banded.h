@@ -108,11 +108,16 @@ typedef struct {
                             run in parallel (0 = default: 2048 for rows, 384 for panels;
                             < 0 = never split) */
     int32_t warmup;      /* warm-up rows of a speculative segment start (0 = default:
-                            24 l + 32 rows in FP32, 48 l + 64 in FP64) */
+                            16 l + 32 rows in FP32, 48 l + 64 in FP64) */
     int32_t blocks_per_sm; /* persistent-grid occupancy (0 = default) */
     int32_t flags;       /* bit 0: never use the shared-memory staged kernels;
                             bit 1: segment length seg_len * warmup / 128 (the same share of
-                            warm-up rows for every bandwidth) */
+                            warm-up rows for every bandwidth);
+                            bit 2: no staged reruns (mismatching segments are only rerun
+                            serially by the verify pass) */
+    int32_t warm_per_l;  /* > 0: warm-up rows = warm_per_l * l + warm_base for bandwidth l
+                            (overrides the defaults; `warmup` > 0 overrides both) */
+    int32_t warm_base;
 } bnd_tuning;
 
 typedef struct bnd_plan bnd_plan;
@@ -213,9 +218,9 @@ bnd_status banded_subset_inverse_vjp(const bnd_plan *plan, const void *L, const 
  *             of Q) and Bbar (nullable) of
  *             <Xbar, X> + <Sbar, S> + sum_i ldbar_i * logdet_i,
  *             composed per Table 1, Alg. 2 and Alg. 4.
- * Needs a plan with k in {1, 2, 3, 4} (BND_EINVAL otherwise): the fused
- * sweeps carry at most 4 right-hand sides; plans with more columns use the
- * separate operators.  The forward writes L, X, S (and keeps L^{-1} B in the
+ * Needs a plan with 1 <= k <= 4, or 1 <= k <= 16 when every instance has
+ * l = 0 or l > 8 (the wide-band kernels take the column count at run time);
+ * BND_EINVAL otherwise.  Plans with more columns use the separate operators.  The forward writes L, X, S (and keeps L^{-1} B in the
  * workspace); the backward reads L, X, S.
  * ------------------------------------------------------------------------- */
 bnd_status banded_gmm_forward(const bnd_plan *plan, const void *Q, const void *B, void *L, void *X,
@@ -252,6 +257,29 @@ bnd_status banded_product_vjp(const bnd_plan *plan, const void *A, int32_t alo, 
                               int32_t transA, const void *B, int32_t blo, int32_t bup,
                               int32_t transB, const void *Cbar, int32_t clo, int32_t cup,
                               void *Abar, void *Bbar, int32_t accumulate, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * S with a banded right-hand side, Alg. 5 (App. B): O = band_{olo,oup}(L^{-1} R)
+ * (trans = 0) or band_{olo,oup}(L^{-T} R) (trans = 1), for a general band R
+ * with bandwidths (rlo, rup); L is lower band l (the plan's per-instance l).
+ * Every band is exact: trans = 0 needs oup >= rup (L^{-1} R has no entries
+ * above that), trans = 1 needs olo >= rlo; BND_EINVAL otherwise.  Each
+ * column of O is an independent triangular solve restricted to the band (the
+ * dependency Alg. 5 walks diagonal by diagonal).  O must not alias L or R.
+ *
+ * Reverse mode, Table 1 ("solve matrix-matrix"): given the forward output O
+ * and its cotangent Obar (on O's band),
+ *   G    = band_{olo,oup}(L^{-T} Obar)   (trans = 0; L^{-1} Obar for trans = 1)
+ *   Rbar = band_{rlo,rup}(G)             (nullable)
+ *   Lbar -= band_l(G O^T)  (trans = 0)   or  band_l(O G^T)  (trans = 1)   (nullable)
+ * G is a caller band pool shaped like O (written; it is also the unprojected
+ * R-bar).  accumulate = 1 adds into Rbar and Lbar.
+ * ------------------------------------------------------------------------- */
+bnd_status banded_solve_band(const bnd_plan *plan, const void *L, const void *R, int32_t rlo, int32_t rup, void *O,
+                             int32_t olo, int32_t oup, int32_t trans, void *stream);
+bnd_status banded_solve_band_vjp(const bnd_plan *plan, const void *L, const void *O, int32_t olo, int32_t oup,
+                                 const void *Obar, int32_t trans, int32_t rlo, int32_t rup, void *G, void *Rbar,
+                                 void *Lbar, int32_t accumulate, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free precision solve (the paper has no counterpart; it exists for

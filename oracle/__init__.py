@@ -64,6 +64,11 @@ def lib():
         L.orc_outer_vjp.restype = None
         L.orc_outer_vjp.argtypes = [_i64, _int, _dp, _i64, _dp, _i64, _dp, _i64, _int, _int,
                                     _dp, _i64, _dp, _i64]
+        L.orc_solve_band.restype = None
+        L.orc_solve_band.argtypes = [_i64, _int, _dp, _i64, _int, _dp, _i64, _int, _int, _dp, _i64, _int, _int]
+        L.orc_solve_band_vjp.restype = None
+        L.orc_solve_band_vjp.argtypes = [_i64, _int, _dp, _i64, _int, _dp, _i64, _int, _int, _dp, _i64,
+                                         _int, _int, _dp, _i64, _dp, _i64]
         L.orc_batch_step.restype = _int
         L.orc_batch_step.argtypes = [_int, C.c_void_p]
         _lib = L
@@ -176,9 +181,31 @@ def outer(M, V, clo, cup):
     return Cm
 
 
+def solve_band(L, R, rlo, rup, trans, olo, oup):
+    """Alg. 5: band_{olo,oup}(L^{-1} R) (trans 0) or band_{olo,oup}(L^{-T} R) (trans 1);
+    R and the result in general band storage."""
+    L, R = _f64(L), _f64(R)
+    n = L.shape[1]
+    O = np.zeros((olo + oup + 1, n))
+    lib().orc_solve_band(n, L.shape[0] - 1, _p(L), n, int(trans), _p(R), n, rlo, rup, _p(O), n, olo, oup)
+    return O
+
+
 # ---------------------------------------------------------------------------
 # Table 1 compositions
 # ---------------------------------------------------------------------------
+
+def solve_band_vjp(L, trans, O, olo, oup, Obar, rlo, rup):
+    """Table 1, solve matrix-matrix, for O = solve_band(...): returns (Rbar, Lbar)."""
+    L, O, Obar = _f64(L), _f64(O), _f64(Obar)
+    n = L.shape[1]
+    l = L.shape[0] - 1
+    Rbar = np.zeros((rlo + rup + 1, n))
+    Lbar = np.zeros_like(L)
+    lib().orc_solve_band_vjp(n, l, _p(L), n, int(trans), _p(O), n, olo, oup, _p(Obar), n, rlo, rup,
+                             _p(Rbar), n, _p(Lbar), n)
+    return Rbar, Lbar
+
 
 def solve_vjp(L, trans, S, Sbar):
     """For S = L^{-1} V (trans 0) or L^{-T} V (trans 1): returns (Vbar, Lbar)."""

@@ -377,6 +377,71 @@ void orc_outer_vjp(i64 n, int k, const double *M, i64 ldm, const double *V, i64 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Solve with a banded right-hand side (Alg. 5): O = band_{olo,oup}(L^{-1} R) */
+/* (trans = 0) or band_{olo,oup}(L^{-T} R) (trans = 1), R a general band     */
+/* (rlo, rup).  Diagonal by diagonal, in the order Alg. 5 gives for the      */
+/* lower solve: offset k = row - column from -oup up to olo (trans = 0; each */
+/* entry uses only entries of its column on smaller offsets), or from olo    */
+/* down to -oup (trans = 1, the mirror order of the upper solve).  Entries   */
+/* outside the computed band are taken as 0; they are exactly 0 when         */
+/* oup >= rup (trans = 0: L^{-1} R has upper bandwidth rup) or olo >= rlo    */
+/* (trans = 1: L^{-T} R has lower bandwidth rlo), which callers must ensure  */
+/* for an exact band.                                                        */
+/* ------------------------------------------------------------------------ */
+void orc_solve_band(i64 n, int l, const double *L, i64 ldl, int trans,
+                    const double *R, i64 ldr, int rlo, int rup,
+                    double *O, i64 ldo, int olo, int oup)
+{
+    for (int r = 0; r < olo + oup + 1; ++r)
+        for (i64 j = 0; j < n; ++j) O[(size_t)r * ldo + j] = 0.0;
+    for (int kk = 0; kk <= olo + oup; ++kk) {
+        int k = trans ? olo - kk : kk - oup;                 /* diagonal offset i - c */
+        for (i64 i = imax(0, k); i <= imin(n - 1, n - 1 + k); ++i) {
+            i64 c = i - k;
+            double rv = (k <= rlo && -k <= rup) ? GB(R, ldr, rup, i, c) : 0.0;
+            double s = 0.0;
+            if (!trans) {                                    /* sum_m L[i, m] O[m, c], m < i */
+                for (i64 m = imax(i - l, 0); m < i; ++m)
+                    if (m - c >= -oup && m - c <= olo) s += LB(L, ldl, i, m) * GB(O, ldo, oup, m, c);
+            } else {                                         /* sum_m L[m, i] O[m, c], m > i */
+                for (i64 m = i + 1; m <= imin(i + l, n - 1); ++m)
+                    if (m - c >= -oup && m - c <= olo) s += LB(L, ldl, m, i) * GB(O, ldo, oup, m, c);
+            }
+            GB(O, ldo, oup, i, c) = (rv - s) / LB(L, ldl, i, i);
+        }
+    }
+}
+
+/* Reverse mode of orc_solve_band (Table 1, "solve matrix-matrix"): for
+ * O = band(L^{-1} R) and its cotangent Obar (both on O's band (olo, oup)):
+ *   G = band_{olo,oup}(L^{-T} Obar),  Rbar = band_R(G),  Lbar -= band_l(G O^T);
+ * for O = band(L^{-T} R):
+ *   G = band_{olo,oup}(L^{-1} Obar),  Rbar = band_R(G),  Lbar -= band_l(O G^T).
+ * Lbar is accumulated (lower band l); Rbar is written on R's band (rlo, rup). */
+void orc_solve_band_vjp(i64 n, int l, const double *L, i64 ldl, int trans,
+                        const double *O, i64 ldo, int olo, int oup, const double *Obar, i64 ldob,
+                        int rlo, int rup, double *Rbar, i64 ldrb, double *Lbar, i64 ldlb)
+{
+    double *G = (double *)malloc((size_t)(olo + oup + 1) * (size_t)n * sizeof(double));
+    double *P = (double *)malloc((size_t)(l + 1) * (size_t)n * sizeof(double));
+    orc_solve_band(n, l, L, ldl, !trans, Obar, ldob, olo, oup, G, n, olo, oup);
+    if (Rbar) {
+        for (int r = 0; r < rlo + rup + 1; ++r)
+            for (i64 j = 0; j < n; ++j) Rbar[(size_t)r * ldrb + j] = 0.0;
+        for (i64 c = 0; c < n; ++c)
+            for (i64 i = imax(c - rup, 0); i <= imin(c + rlo, n - 1); ++i)
+                if (i - c <= olo && c - i <= oup) GB(Rbar, ldrb, rup, i, c) = GB(G, n, oup, i, c);
+    }
+    if (Lbar) {
+        if (!trans) orc_product(n, G, n, olo, oup, 0, O, ldo, olo, oup, 1, P, n, l, 0);
+        else        orc_product(n, O, ldo, olo, oup, 0, G, n, olo, oup, 1, P, n, l, 0);
+        for (int d = 0; d <= l; ++d)
+            for (i64 j = 0; j + d < n; ++j) Lbar[(size_t)d * ldlb + j] -= P[(size_t)d * n + j];
+    }
+    free(G); free(P);
+}
+
+/* ------------------------------------------------------------------------ */
 /* The uneven-batch step: for each instance                                  */
 /*   forward : L = C(Q), ld = log det Q, X = Q^{-1} B = S(L^T, S(L, B)),     */
 /*             S = I(L)                                                      */

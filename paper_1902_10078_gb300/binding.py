@@ -27,6 +27,7 @@ EXPORTS = [
     "banded_subset_inverse", "banded_subset_inverse_vjp",
     "banded_gmm_forward", "banded_gmm_backward",
     "banded_product", "banded_outer", "banded_matvec", "banded_product_vjp",
+    "banded_solve_band", "banded_solve_band_vjp",
     "banded_solve_precision_noalloc",
     "bnd_version",
 ]
@@ -44,7 +45,8 @@ class bnd_inst(C.Structure):
 
 
 class bnd_tuning(C.Structure):
-    _fields_ = [("seg_len", C.c_int64), ("warmup", C.c_int32), ("blocks_per_sm", C.c_int32), ("flags", C.c_int32)]
+    _fields_ = [("seg_len", C.c_int64), ("warmup", C.c_int32), ("blocks_per_sm", C.c_int32), ("flags", C.c_int32),
+                ("warm_per_l", C.c_int32), ("warm_base", C.c_int32)]
 
 
 _lib = None
@@ -77,6 +79,9 @@ def lib():
         "banded_subset_inverse": (_i32, [_vp, _vp, _vp, _vp]),
         "banded_subset_inverse_vjp": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
         "banded_gmm_forward": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "banded_solve_band": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _i32, _i32, _i32, _vp]),
+        "banded_solve_band_vjp": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _i32,
+                                         _vp]),
         "banded_gmm_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "banded_product": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _i32, _i32, _i32, _vp, _i32, _i32, _i32, _vp]),
         "banded_outer": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _vp]),
@@ -129,7 +134,8 @@ def bnd_plan_create(dtype: int, insts, k: int, tuning=None):
     tp = None
     if tuning is not None:
         tp = C.pointer(bnd_tuning(int(tuning.get("seg_len", 0)), int(tuning.get("warmup", 0)),
-                                  int(tuning.get("blocks_per_sm", 0)), int(tuning.get("flags", 0))))
+                                  int(tuning.get("blocks_per_sm", 0)), int(tuning.get("flags", 0)),
+                                  int(tuning.get("warm_per_l", 0)), int(tuning.get("warm_base", 0))))
     h = _vp()
     _check("bnd_plan_create", lib().bnd_plan_create(C.byref(h), dtype, len(insts), arr, int(k), tp))
     return h.value
@@ -235,3 +241,17 @@ def banded_solve_precision_noalloc(dtype: int, n: int, l: int, L, ld: int, b, x,
     """x = (L L^T)^{-1} b for one instance without any allocation (fixed library scratch)."""
     _check("banded_solve_precision_noalloc",
            lib().banded_solve_precision_noalloc(int(dtype), int(n), int(l), _p(L), int(ld), _p(b), _p(x), _s(stream)))
+
+
+def banded_solve_band(plan, L, R, rlo: int, rup: int, O, olo: int, oup: int, trans: int, stream=None):
+    """Alg. 5: O = band_{olo,oup}(op(L)^{-1} R)."""
+    _check("banded_solve_band", lib().banded_solve_band(plan, _p(L), _p(R), int(rlo), int(rup), _p(O), int(olo),
+                                                        int(oup), int(trans), _s(stream)))
+
+
+def banded_solve_band_vjp(plan, L, O, olo: int, oup: int, Obar, trans: int, rlo: int, rup: int, G, Rbar, Lbar,
+                          accumulate: int = 0, stream=None):
+    """Table 1 (solve matrix-matrix) adjoint of banded_solve_band."""
+    _check("banded_solve_band_vjp", lib().banded_solve_band_vjp(plan, _p(L), _p(O), int(olo), int(oup), _p(Obar),
+                                                                int(trans), int(rlo), int(rup), _p(G), _p(Rbar),
+                                                                _p(Lbar), int(accumulate), _s(stream)))

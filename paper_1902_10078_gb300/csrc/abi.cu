@@ -3,6 +3,7 @@
 
 #include "common.cuh"
 #include "products.cuh"
+#include "sweep_cta.cuh"
 #include "sweep_impl.cuh"
 
 using namespace bnd;
@@ -12,6 +13,11 @@ namespace {
 inline cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 
 inline bnd_status ok_or(cudaError_t e) { return e == cudaSuccess ? BND_OK : BND_ECUDA; }
+
+// Right-hand sides one sweep carries: 4 in the register-window kernels; 16 when
+// every instance is of the wide class (l = 0 or l above the register-window
+// limit), whose kernels take the column count at run time.
+int rhs_block(const bnd_plan *p) { return p->class_task0[1] == p->ntasks ? kCtaMaxK : kMaxK; }
 
 bnd_status check_plan(const bnd_plan *p) {
     if (!p || !p->bound) return BND_EINVAL;
@@ -86,8 +92,9 @@ bnd_status cholesky_t(const bnd_plan *p, const void *Q, void *L, double *logdet,
 
 template <typename T>
 bnd_status solve_t(const bnd_plan *p, const void *L, const void *B, void *X, int mode, cudaStream_t s) {
-    for (int r0 = 0; r0 < p->k; r0 += kMaxK) {
-        const int kk = (p->k - r0) < kMaxK ? (p->k - r0) : kMaxK;
+    const int kb = rhs_block(p);
+    for (int r0 = 0; r0 < p->k; r0 += kb) {
+        const int kk = (p->k - r0) < kb ? (p->k - r0) : kb;
         SweepArgs<T> A = blank_args<T>(p);
         A.Lin = (const T *)L; A.rhs0 = r0; A.kk = kk;
         if (mode == 0 || mode == 1) {
@@ -294,7 +301,7 @@ extern "C" bnd_status banded_subset_inverse_vjp(const bnd_plan *p, const void *L
 extern "C" bnd_status banded_gmm_forward(const bnd_plan *p, const void *Q, const void *B, void *L, void *X,
                                          void *Sout, double *logdet, int32_t *info, void *stream) {
     BND_TRY(check_plan(p));
-    if (p->k < 1 || p->k > kMaxK || !info) return BND_EINVAL;
+    if (p->k < 1 || p->k > rhs_block(p) || !info) return BND_EINVAL;
     BND_TRY(check_ptr(p, Q)); BND_TRY(check_ptr(p, B)); BND_TRY(check_ptr(p, L));
     BND_TRY(check_ptr(p, X)); BND_TRY(check_ptr(p, Sout));
     return BND_DISPATCH(gmm_forward_t<float>(p, Q, B, L, X, Sout, logdet, info, S(stream)),
@@ -305,7 +312,7 @@ extern "C" bnd_status banded_gmm_backward(const bnd_plan *p, const void *L, cons
                                           const void *Xbar, const void *Sbar, const double *ldbar, void *Qbar,
                                           void *Bbar, void *stream) {
     BND_TRY(check_plan(p));
-    if (p->k < 1 || p->k > kMaxK) return BND_EINVAL;
+    if (p->k < 1 || p->k > rhs_block(p)) return BND_EINVAL;
     BND_TRY(check_ptr(p, L)); BND_TRY(check_ptr(p, X)); BND_TRY(check_ptr(p, Sm));
     BND_TRY(check_ptr(p, Xbar)); BND_TRY(check_ptr(p, Sbar)); BND_TRY(check_ptr(p, Qbar));
     BND_TRY(check_ptr(p, Bbar, false));
@@ -374,6 +381,62 @@ extern "C" bnd_status banded_product_vjp(const bnd_plan *p, const void *Am, int3
     return BND_DISPATCH(
         product_vjp_t<float>(p, Am, alo, aup, transA != 0, Bm, blo, bup, transB != 0, Cbar, clo, cup, Abar, Bbar, accumulate != 0, S(stream)),
         product_vjp_t<double>(p, Am, alo, aup, transA != 0, Bm, blo, bup, transB != 0, Cbar, clo, cup, Abar, Bbar, accumulate != 0, S(stream)));
+}
+
+// Alg. 5 and its Table 1 adjoint ("solve matrix-matrix")
+template <typename T>
+static bnd_status solve_band_t(const bnd_plan *p, const void *L, const void *R, int rlo, int rup, void *O, int olo,
+                               int oup, int trans, cudaStream_t s) {
+    SolveBandArgs<T> A{};
+    A.L = (const T *)L; A.R = (const T *)R; A.O = (T *)O;
+    A.rlo = rlo; A.rup = rup; A.olo = olo; A.oup = oup; A.trans = trans;
+    return ok_or(launch_solve_band<T>(p, A, s));
+}
+
+template <typename T>
+static bnd_status solve_band_vjp_t(const bnd_plan *p, const void *L, const void *O, int olo, int oup, const void *Obar,
+                                   int trans, int rlo, int rup, void *G, void *Rbar, void *Lbar, int acc,
+                                   cudaStream_t s) {
+    BND_TRY(solve_band_t<T>(p, L, Obar, olo, oup, G, olo, oup, !trans, s));       // G = op(L)^{-T} Obar
+    if (Rbar) {
+        BandCopyArgs<T> A{};
+        A.src = (const T *)G; A.dst = (T *)Rbar; A.slo = olo; A.sup = oup; A.dlo = rlo; A.dup = rup; A.acc = acc;
+        BND_CUDA(launch_band_copy<T>(p, A, s));
+    }
+    if (Lbar) {            // Lbar -= band_l(G O^T)  (or band_l(O G^T) for the transposed solve)
+        if (!trans) BND_TRY(product_t<T>(p, G, olo, oup, 0, O, olo, oup, 1, Lbar, -1, 0, acc, T(-1), s));
+        else BND_TRY(product_t<T>(p, O, olo, oup, 0, G, olo, oup, 1, Lbar, -1, 0, acc, T(-1), s));
+    }
+    return BND_OK;
+}
+
+static bool solve_band_shape_ok(int rlo, int rup, int olo, int oup, int trans) {
+    if (!band_ok(rlo, rup) || !band_ok(olo, oup) || rlo < 0 || olo < 0) return false;
+    return trans ? olo >= rlo : oup >= rup;           // the computed band holds every nonzero it needs
+}
+
+extern "C" bnd_status banded_solve_band(const bnd_plan *p, const void *L, const void *R, int32_t rlo, int32_t rup,
+                                        void *O, int32_t olo, int32_t oup, int32_t trans, void *stream) {
+    BND_TRY(check_plan(p));
+    if (!solve_band_shape_ok(rlo, rup, olo, oup, trans != 0)) return BND_EINVAL;
+    BND_TRY(check_ptr(p, L)); BND_TRY(check_ptr(p, R)); BND_TRY(check_ptr(p, O));
+    if (O == R || O == L) return BND_EINVAL;
+    return BND_DISPATCH(solve_band_t<float>(p, L, R, rlo, rup, O, olo, oup, trans != 0, S(stream)),
+                        solve_band_t<double>(p, L, R, rlo, rup, O, olo, oup, trans != 0, S(stream)));
+}
+
+extern "C" bnd_status banded_solve_band_vjp(const bnd_plan *p, const void *L, const void *O, int32_t olo, int32_t oup,
+                                            const void *Obar, int32_t trans, int32_t rlo, int32_t rup, void *G,
+                                            void *Rbar, void *Lbar, int32_t accumulate, void *stream) {
+    BND_TRY(check_plan(p));
+    if (!solve_band_shape_ok(rlo, rup, olo, oup, trans != 0)) return BND_EINVAL;
+    BND_TRY(check_ptr(p, L)); BND_TRY(check_ptr(p, O)); BND_TRY(check_ptr(p, Obar)); BND_TRY(check_ptr(p, G));
+    BND_TRY(check_ptr(p, Rbar, false)); BND_TRY(check_ptr(p, Lbar, false));
+    if (G == O || G == Obar || G == L || (Rbar && (Rbar == G || Rbar == Obar)) || (Lbar && Lbar == G))
+        return BND_EINVAL;
+    return BND_DISPATCH(
+        solve_band_vjp_t<float>(p, L, O, olo, oup, Obar, trans != 0, rlo, rup, G, Rbar, Lbar, accumulate != 0, S(stream)),
+        solve_band_vjp_t<double>(p, L, O, olo, oup, Obar, trans != 0, rlo, rup, G, Rbar, Lbar, accumulate != 0, S(stream)));
 }
 
 extern "C" const char *bnd_version(void) { return "banded-gb300 0.1 (sm_103a)"; }

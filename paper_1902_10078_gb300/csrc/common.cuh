@@ -57,8 +57,11 @@ struct PlanDev {
     const InstDev *inst;
     const Chain *chains;
     const Task *tasks;
-    const int64_t *tile_prefix;  // products: prefix of 256-column tiles per instance
+    const int64_t *tile_prefix;  // products: prefix of 256-column tiles per instance (rows plans) or of
+                                 // 8-column tiles per panel group (panel plans: 32 lanes x 8 columns)
     int64_t ntiles;
+    const int32_t *group_first;  // panel plans: first instance of each group (ngroups + 1 entries)
+    int32_t ngroups;             // 0 for rows / strided plans
     int32_t ntasks;
     int32_t count;
     int64_t nchains;
@@ -76,6 +79,12 @@ struct PlanDev {
     void *band_tmp;          // band-shaped scratch pool (fused backward intermediate)
     void *band_tmp2;         // band-shaped scratch pools of the generic (wide band) path
     void *band_tmp3;
+    // staged reruns of segments whose speculative start state was wrong
+    const int32_t *seg_chain;  // per global segment: index of the chain that runs it
+    uint32_t *rerun_cnt;       // per bandwidth class: tasks queued for a rerun
+    int32_t *rerun_list;       // task ids, class c's queue at [class_task0[c], class_task0[c+1])
+    uint32_t *task_flag;       // per task: queued (1) or not (0)
+    uint8_t *chain_flag;       // per chain: rerun this lane (1) or not (0)
 };
 
 __host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -111,21 +120,27 @@ struct bnd_plan {
     bnd::Task *tasks;
     int64_t *tile_prefix;
     int64_t ntiles;
+    int32_t *group_first;      // panel plans: groups (ngroups + 1 entries)
+    int32_t ngroups;
     int32_t has_generic;       // some instance runs the generic (any-bandwidth) path
     // tasks are grouped by bandwidth class: class 0 = generic (l = 0 or l > kRegMaxL),
     // class c = bandwidth c; class c owns tasks [class_task0[c], class_task0[c+1])
     int32_t class_task0[bnd::kRegMaxL + 2];
     int32_t layout;            // kLayoutRows, kLayoutPanels or kLayoutStrided
     int32_t staged_ok;         // every offset / stride allows 16-byte tiles
+    int32_t warm_per_l, warm_base;   // tuning: warm-up rows = warm_per_l * l + warm_base (if > 0)
     int32_t force_direct;      // tuning: never use the staged kernels
     int32_t seg_by_warm;       // tuning: segment length proportional to the warm-up
+    int32_t no_staged_rerun;   // tuning: leave every mismatching segment to the serial verify pass
     cudaStream_t side[bnd::kRegMaxL + 1];
     cudaEvent_t ev_fork;
     cudaEvent_t ev_join[bnd::kRegMaxL + 1];
     int32_t streams_ready;
     // workspace layout (byte offsets)
     size_t off_inst, off_chains, off_tasks, off_tiles, off_counters, off_snap, off_logdet, off_info,
-        off_rhs_tmp, off_rhs_tmp2, off_band_tmp, off_band_tmp2, off_band_tmp3, ws_bytes;
+        off_rhs_tmp, off_rhs_tmp2, off_band_tmp, off_band_tmp2, off_band_tmp3, off_seg_chain, off_rerun_cnt, off_groups,
+        off_rerun_list, off_task_flag, off_chain_flag, ws_bytes;
+    int32_t *seg_chain;        // host table uploaded at bind
     // bound workspace
     void *ws;
     bnd::PlanDev dev;

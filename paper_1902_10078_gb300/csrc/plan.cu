@@ -22,14 +22,22 @@ namespace {
 // by the latency of the per-row recurrence and need many resident chains.
 constexpr int64_t kDefaultSegLenRows = 2048;
 constexpr int64_t kDefaultSegLenPanels = 384;
+// A batch too small to give the GPU about this many chains at the default
+// length (a single long chain, a few instances) is cut into shorter segments,
+// down to kMinSegLen rows: its sweeps are bound by the per-row latency, and the
+// time of a sweep is that of one chain, segment plus warm-up rows.
+constexpr int64_t kTargetChains = 16384;
+constexpr int64_t kMinSegLen = 32;
 
 // Default warm-up of a speculative segment start.  The cold-started state
 // forgets its start at a rate per block of l rows, so the warm-up grows with
-// l; measured bit-exact convergence on the uneven batch needed about 16 l rows
-// in FP32 (l = 7: 64 rows fail, 128 converge); the defaults keep a margin, and
-// FP64 needs roughly twice the distance to reach its smaller rounding unit.
+// l.  Measured on the uneven batch (FP32, 384-row panel segments, staged
+// reruns on): 16 l + 32 rows converged everywhere and was the fastest;
+// 12 l + 32 left 7 of 162k segments to rerun, 8 l + 32 left 1671 (each rerun
+// pass costs more than the warm-up rows it saves).  FP64 needs roughly twice
+// the distance to reach its smaller rounding unit.
 int64_t default_warm(bnd_dtype dt, int l) {
-    const int64_t w = dt == BND_F32 ? 24 * (int64_t)l + 32 : 48 * (int64_t)l + 64;
+    const int64_t w = dt == BND_F32 ? 16 * (int64_t)l + 32 : 48 * (int64_t)l + 64;
     return (w + 3) / 4 * 4;
 }
 constexpr int32_t kMaxBand = 1024;
@@ -123,6 +131,11 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         if (tuning->blocks_per_sm > 0) p->blocks_per_sm = tuning->blocks_per_sm;
         p->force_direct = (tuning->flags & 1) != 0;
         p->seg_by_warm = (tuning->flags & 2) != 0;
+        p->no_staged_rerun = (tuning->flags & 4) != 0;
+        if (tuning->warm_per_l > 0) {
+            p->warm_per_l = tuning->warm_per_l;
+            p->warm_base = tuning->warm_base > 0 ? tuning->warm_base : 0;
+        }
     }
     const int64_t tw = 16 / (int64_t)esz;                 // elements per 16-byte tile
     p->staged_ok = 1;
@@ -139,7 +152,22 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
                 for (int32_t i = groups[g]; i < groups[g + 1]; ++i) group_of[(size_t)i] = (int32_t)g;
     }
     const bool panels = p->layout == kLayoutPanels;
-    if (p->seg_len == 0) p->seg_len = panels ? kDefaultSegLenPanels : kDefaultSegLenRows;
+    if (p->seg_len == 0) {
+        p->seg_len = panels ? kDefaultSegLenPanels : kDefaultSegLenRows;
+        // rows that run as lanes: every instance (rows), or 32 lanes of each group's longest n (panels)
+        int64_t lane_rows = 0;
+        if (panels) {
+            for (size_t g = 0; g + 1 < groups.size(); ++g) {
+                int64_t gn = 0;
+                for (int32_t i = groups[g]; i < groups[g + 1]; ++i) gn = std::max(gn, inst[i].n);
+                lane_rows += gn * kPanelLanes;
+            }
+        } else {
+            for (int32_t i = 0; i < count; ++i) lane_rows += inst[i].n;
+        }
+        if (lane_rows / p->seg_len < kTargetChains)
+            p->seg_len = std::max<int64_t>(kMinSegLen, (lane_rows / kTargetChains + 3) / 4 * 4);
+    }
 
     std::vector<InstDev> idev((size_t)count);
     int64_t nsegs = 0;
@@ -153,7 +181,9 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         D.cs = col_stride(I);
         const bool reg = I.l >= 1 && I.l <= kRegMaxL;
         if (!reg) has_generic = true;
-        D.warm = p->warm > 0 ? ((int64_t)p->warm + 3) / 4 * 4 : default_warm(dtype, I.l);
+        if (p->warm > 0) D.warm = ((int64_t)p->warm + 3) / 4 * 4;
+        else if (p->warm_per_l > 0) D.warm = ((int64_t)p->warm_per_l * I.l + p->warm_base + 3) / 4 * 4;
+        else D.warm = default_warm(dtype, I.l);
         // segment length: the same for every bandwidth, or (flag) scaled with the warm-up so
         // that every bandwidth pays the same fraction of extra rows (seg_len at 128 warm-up rows)
         int64_t seg_len = p->seg_len;
@@ -291,12 +321,37 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         p->tasks[t].l = tt[t].l;
         for (int c = 0; c < kWarp; ++c) p->chains[t * kWarp + c] = tt[t].c[(size_t)c];
     }
-    // product tile prefix (256 columns per tile)
-    p->tile_prefix = (int64_t *)std::malloc(sizeof(int64_t) * ((size_t)count + 1));
-    if (!p->tile_prefix) { bnd_plan_destroy(p); return BND_EINVAL; }
-    p->tile_prefix[0] = 0;
-    for (int32_t i = 0; i < count; ++i) p->tile_prefix[i + 1] = p->tile_prefix[i] + (idev[(size_t)i].n + 255) / 256;
-    p->ntiles = p->tile_prefix[count];
+    // chain running each global segment (staged reruns address segments through it)
+    p->seg_chain = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(1, (size_t)nsegs));
+    if (!p->seg_chain) { bnd_plan_destroy(p); return BND_EINVAL; }
+    for (int64_t g = 0; g < nsegs; ++g) p->seg_chain[g] = -1;
+    for (int64_t c = 0; c < p->nchains; ++c) {
+        const Chain &ch = p->chains[c];
+        if (ch.inst >= 0) p->seg_chain[idev[(size_t)ch.inst].seg0 + ch.seg] = (int32_t)c;
+    }
+    // product tiles: 256 columns of one instance (rows plans), or 8 columns of the 32 lanes of
+    // a panel group (panel plans: a warp reads one column of the group, 32 adjacent elements)
+    if (panels) {
+        p->ngroups = (int32_t)groups.size() - 1;
+        p->group_first = (int32_t *)std::malloc(sizeof(int32_t) * groups.size());
+        p->tile_prefix = (int64_t *)std::malloc(sizeof(int64_t) * groups.size());
+        if (!p->group_first || !p->tile_prefix) { bnd_plan_destroy(p); return BND_EINVAL; }
+        p->tile_prefix[0] = 0;
+        for (int32_t g = 0; g <= p->ngroups; ++g) p->group_first[g] = groups[(size_t)g];
+        for (int32_t g = 0; g < p->ngroups; ++g) {
+            int64_t gn = 0;
+            for (int32_t i = groups[(size_t)g]; i < groups[(size_t)g + 1]; ++i) gn = std::max(gn, inst[i].n);
+            p->tile_prefix[g + 1] = p->tile_prefix[g] + (gn + 7) / 8;
+        }
+        p->ntiles = p->tile_prefix[p->ngroups];
+    } else {
+        p->ngroups = 0;
+        p->tile_prefix = (int64_t *)std::malloc(sizeof(int64_t) * ((size_t)count + 1));
+        if (!p->tile_prefix) { bnd_plan_destroy(p); return BND_EINVAL; }
+        p->tile_prefix[0] = 0;
+        for (int32_t i = 0; i < count; ++i) p->tile_prefix[i + 1] = p->tile_prefix[i] + (idev[(size_t)i].n + 255) / 256;
+        p->ntiles = p->tile_prefix[count];
+    }
     p->has_generic = has_generic ? 1 : 0;
 
     // workspace layout
@@ -305,7 +360,8 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->off_inst = take(sizeof(InstDev) * (size_t)count);
     p->off_chains = take(sizeof(Chain) * (size_t)p->nchains);
     p->off_tasks = take(sizeof(Task) * (size_t)p->ntasks);
-    p->off_tiles = take(sizeof(int64_t) * ((size_t)count + 1));
+    p->off_tiles = take(sizeof(int64_t) * ((size_t)std::max(count, p->ngroups) + 1));
+    p->off_groups = take(sizeof(int32_t) * ((size_t)p->ngroups + 1));
     p->off_counters = take(sizeof(unsigned int) * 2 * kNumSweepKinds);
     p->off_snap = take(esz * (size_t)nsegs * 2 * (size_t)p->snap_words);
     p->off_logdet = take(sizeof(double) * (size_t)nsegs);
@@ -315,6 +371,11 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->off_band_tmp = take(esz * (size_t)band_extent);
     p->off_band_tmp2 = take(has_generic ? esz * (size_t)band_extent : 0);
     p->off_band_tmp3 = take(has_generic ? esz * (size_t)band_extent : 0);
+    p->off_seg_chain = take(sizeof(int32_t) * (size_t)nsegs);
+    p->off_rerun_cnt = take(sizeof(uint32_t) * (kRegMaxL + 1));
+    p->off_rerun_list = take(sizeof(int32_t) * (size_t)p->ntasks);
+    p->off_task_flag = take(sizeof(uint32_t) * (size_t)p->ntasks);
+    p->off_chain_flag = take((size_t)p->nchains);
     p->ws_bytes = o;
     *out = p;
     return BND_OK;
@@ -344,6 +405,8 @@ extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void
     d.nchains = p->nchains;
     d.nsegs = p->nsegs;
     d.ntiles = p->ntiles;
+    d.ngroups = p->ngroups;
+    d.group_first = (const int32_t *)(base + p->off_groups);
     d.k = p->k;
     d.warm = p->warm;
     d.counters = (unsigned int *)(base + p->off_counters);
@@ -356,6 +419,11 @@ extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void
     d.band_tmp = base + p->off_band_tmp;
     d.band_tmp2 = base + p->off_band_tmp2;
     d.band_tmp3 = base + p->off_band_tmp3;
+    d.seg_chain = (const int32_t *)(base + p->off_seg_chain);
+    d.rerun_cnt = (uint32_t *)(base + p->off_rerun_cnt);
+    d.rerun_list = (int32_t *)(base + p->off_rerun_list);
+    d.task_flag = (uint32_t *)(base + p->off_task_flag);
+    d.chain_flag = (uint8_t *)(base + p->off_chain_flag);
     cudaError_t e = cudaSuccess;
     if (!p->streams_ready) {
         for (int c = 0; c <= kRegMaxL && e == cudaSuccess; ++c) {
@@ -369,8 +437,16 @@ extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void
     if (p->count) e = cudaMemcpyAsync(base + p->off_inst, p->inst, sizeof(InstDev) * (size_t)p->count, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->nchains) e = cudaMemcpyAsync(base + p->off_chains, p->chains, sizeof(Chain) * (size_t)p->nchains, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->ntasks) e = cudaMemcpyAsync(base + p->off_tasks, p->tasks, sizeof(Task) * (size_t)p->ntasks, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + p->off_tiles, p->tile_prefix, sizeof(int64_t) * ((size_t)p->count + 1), cudaMemcpyHostToDevice, s);
+    const size_t ntab = (size_t)(p->ngroups > 0 ? p->ngroups : p->count) + 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + p->off_tiles, p->tile_prefix, sizeof(int64_t) * ntab, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && p->ngroups > 0)
+        e = cudaMemcpyAsync(base + p->off_groups, p->group_first, sizeof(int32_t) * ((size_t)p->ngroups + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + p->off_counters, 0, sizeof(unsigned int) * 2 * kNumSweepKinds, s);
+    if (e == cudaSuccess && p->nsegs)
+        e = cudaMemcpyAsync(base + p->off_seg_chain, p->seg_chain, sizeof(int32_t) * (size_t)p->nsegs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + p->off_rerun_cnt, 0, sizeof(uint32_t) * (kRegMaxL + 1), s);
+    if (e == cudaSuccess && p->ntasks) e = cudaMemsetAsync(base + p->off_task_flag, 0, sizeof(uint32_t) * (size_t)p->ntasks, s);
+    if (e == cudaSuccess && p->nchains) e = cudaMemsetAsync(base + p->off_chain_flag, 0, (size_t)p->nchains, s);
     // pageable sources: make sure the copies have consumed the host tables before returning
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return BND_ECUDA;
@@ -391,6 +467,8 @@ extern "C" void bnd_plan_destroy(bnd_plan *p) {
     std::free(p->chains);
     std::free(p->tasks);
     std::free(p->tile_prefix);
+    std::free(p->group_first);
+    std::free(p->seg_chain);
     delete p;
 }
 

@@ -32,7 +32,23 @@ struct MatvecArgs {
     T alpha;
 };
 
+template <typename T>
+struct SolveBandArgs {
+    const T *L; const T *R; T *O;      // L: lower band l (per instance); R, O: general bands
+    int rlo, rup, olo, oup;
+    int trans;
+};
+
+template <typename T>
+struct BandCopyArgs {                  // dst (dlo, dup) (+)= src (slo, sup) on dst's band
+    const T *src; T *dst;
+    int slo, sup, dlo, dup;
+    int acc;
+};
+
 template <typename T> cudaError_t launch_product(const bnd_plan *p, const ProdArgs<T> &A, cudaStream_t s);
+template <typename T> cudaError_t launch_solve_band(const bnd_plan *p, const SolveBandArgs<T> &A, cudaStream_t s);
+template <typename T> cudaError_t launch_band_copy(const bnd_plan *p, const BandCopyArgs<T> &A, cudaStream_t s);
 template <typename T> cudaError_t launch_outer(const bnd_plan *p, const OuterArgs<T> &A, cudaStream_t s);
 template <typename T> cudaError_t launch_matvec(const bnd_plan *p, const MatvecArgs<T> &A, cudaStream_t s);
 template <typename T> cudaError_t launch_band_add(const bnd_plan *p, const T *src, T *dst, cudaStream_t s);

@@ -164,6 +164,13 @@ template <> struct LogSum<float> {
 // Start modes of a chain run.
 enum : int { RUN_COLD = 0, RUN_EXACT = 1 };
 
+// Interior tiles of bandwidths up to this value unroll their rows (the step
+// body is instantiated once per row of the tile); wider bands keep one copy of
+// the body, whose size otherwise overflows the instruction cache.
+#ifndef BND_INTERIOR_UNROLL_MAX_L
+#define BND_INTERIOR_UNROLL_MAX_L 8
+#endif
+
 // ===========================================================================
 // Register-window forward sweep: CHOL [+ SOLVE], SOLVE, ALG4 [+ SOLVE]
 // Input streams:  [0, L]      Q (CHOL) or L, diagonal d, column j
@@ -595,8 +602,13 @@ __device__ void run_fwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
         // interior tile: every column of the tile and every streamed column (offsets <= L + 1) is inside the matrix
         const bool interior = jt >= j0 && jt + TW - 1 <= jend && jt + TW + 2 * L + 1 < c.n;
         if (interior) {
+            if constexpr (L <= BND_INTERIOR_UNROLL_MAX_L) {
 #pragma unroll
-            for (int u = 0; u < TW; ++u) s.template step<false>(io, A, c, jt + u, u, has_out, ld, info);
+                for (int u = 0; u < TW; ++u) s.template step<false>(io, A, c, jt + u, u, has_out, ld, info);
+            } else {
+#pragma unroll 1
+                for (int u = 0; u < TW; ++u) s.template step<false>(io, A, c, jt + u, u, has_out, ld, info);
+            }
         } else {
             for (int u = 0; u < TW; ++u) {
                 const int64_t j = jt + u;
@@ -647,8 +659,13 @@ __device__ void run_bwd_reg(const PlanDev &P, const SweepArgs<T> &A, const Chain
         // interior tile: all its columns inside [a, j0], rows below n, window columns >= 0
         const bool interior = jt >= c.a && jt + TW - 1 <= j0 && jt + TW + L < c.n && jt - 1 - L >= 0;
         if (interior) {
+            if constexpr (L <= BND_INTERIOR_UNROLL_MAX_L) {
 #pragma unroll
-            for (int u = TW - 1; u >= 0; --u) s.template step<false>(io, A, c, jt + u, u, has_out);
+                for (int u = TW - 1; u >= 0; --u) s.template step<false>(io, A, c, jt + u, u, has_out);
+            } else {
+#pragma unroll 1
+                for (int u = TW - 1; u >= 0; --u) s.template step<false>(io, A, c, jt + u, u, has_out);
+            }
         } else {
             for (int u = TW - 1; u >= 0; --u) {
                 const int64_t j = jt + u;

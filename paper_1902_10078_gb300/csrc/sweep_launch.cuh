@@ -7,6 +7,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "sweep_cta.cuh"
 #include "sweep_impl.cuh"
 #include "sweep_wide.cuh"
 
@@ -115,6 +116,13 @@ __device__ __forceinline__ ChainCtx idle_ctx() {
     return c;
 }
 
+// Exact start state of a rerun segment: the end snapshot of the segment before
+// it in sweep order (forward sweeps: the one above; backward: the one below).
+template <typename T, bool FWD>
+__device__ __forceinline__ const T *exact_start(const PlanDev &P, const ChainCtx &c) {
+    return snap_ptr<T>(P, FWD ? c.gseg - 1 : c.gseg + 1, 1);
+}
+
 // Staged per-bandwidth launcher: defined in sweep_staged.cuh and explicitly
 // instantiated per bandwidth in its own translation unit (sweep_staged_l*.cu),
 // so the large staged kernels compile in parallel.
@@ -140,9 +148,39 @@ wide_kernel(PlanDev P, SweepArgs<T> A, int64_t chain0, int64_t nchains) {
     else run_bwd_wide<T, FL>(P, A, c, lane);
 }
 
+// Block-per-chain kernel of the generic bandwidth class: the computed window
+// in shared memory (sweep_cta.cuh).  Used when the window of the widest
+// instance fits the per-block shared memory.
+
+template <typename T, int K, int FL, bool FWD>
+__global__ void __launch_bounds__(kCtaThreads) cta_kernel(PlanDev P, SweepArgs<T> A, int64_t chain0, int64_t nchains) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t w = blockIdx.x;
+    if (w >= nchains) return;
+    const Chain ch = P.chains[chain0 + w];
+    if (ch.inst < 0) return;
+    const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    if constexpr (FWD) run_fwd_cta<T, FL>(P, A, c, sm);
+    else run_bwd_cta<T, FL>(P, A, c, sm);
+}
+
 template <typename T, int K, int FL, bool FWD>
 static cudaError_t launch_wide(const bnd_plan *p, const SweepArgs<T> &A, int32_t t0, int32_t nt, cudaStream_t s) {
     if (nt <= 0) return cudaSuccess;
+    const size_t cta_bytes = sizeof(T) * (size_t)cta_smem_elems(p->max_l);
+    if (cta_fits<T>(p->max_l)) {
+        static PerDeviceSlots attr;
+        const int ok = per_device(attr, [] {
+            return cudaFuncSetAttribute(cta_kernel<T, K, FL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kCtaSmemLimit) == cudaSuccess ? 1 : -1;
+        });
+        if (ok <= 0) return cudaErrorInvalidValue;
+        const int64_t nch = (int64_t)nt * kWarp;
+        cta_kernel<T, K, FL, FWD><<<(unsigned)nch, kCtaThreads, cta_bytes, s>>>(p->dev, A, (int64_t)t0 * kWarp, nch);
+        return cudaGetLastError();
+    }
+    // windows too large for shared memory: one warp per chain, windows in global memory
     const int64_t nch = (int64_t)nt * kWarp;
     const int64_t blocks = (nch + kWideWarpsPerBlock - 1) / kWideWarpsPerBlock;
     wide_kernel<T, K, FL, FWD><<<(unsigned)blocks, kWarp * kWideWarpsPerBlock, 0, s>>>(p->dev, A, (int64_t)t0 * kWarp,

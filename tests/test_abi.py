@@ -190,3 +190,20 @@ def test_noalloc_rejects_misaligned_and_bad_sizes(lib):
         with pytest.raises(B.BandedError) as e:
             B.banded_solve_precision_noalloc(B.BND_F64, n, l, _BASE, ld, _BASE + 4096, _BASE + 8192, stream=0)
         assert e.value.status == 1
+
+
+def test_small_batches_get_short_segments(lib):
+    # one long chain cannot fill the GPU at the 2048-row default: the default length
+    # drops so that about 16k chains run, but never below 32 rows
+    p = B.bnd_plan_create(B.BND_F32, _insts([100000], [3]), 1)
+    try:
+        assert B.bnd_plan_chains(p) == round(100000 / 32)
+    finally:
+        B.bnd_plan_destroy(p)
+    # a batch with enough rows keeps the 2048-row default
+    ns = [60000] * 600
+    p = B.bnd_plan_create(B.BND_F32, _insts(ns, [2] * 600), 1)
+    try:
+        assert B.bnd_plan_chains(p) == 600 * round(60000 / 2048)
+    finally:
+        B.bnd_plan_destroy(p)

@@ -2,7 +2,7 @@
 
 The whole 4096-instance batch (n log-uniform in [1000, 65536], l in
 {1, 2, 3, 5, 7}, k = 4, FP32) in the 32-lane panel arrangement, planned with
-the library defaults (384-row segments, 24 l + 32 warm-up rows: the launch
+the library defaults (384-row segments, 16 l + 32 warm-up rows: the launch
 configuration bench.py times), runs one fused forward + backward step.
 Every instance must factor (info = 0); a sample of instances -- the longest
 one of every bandwidth plus a seeded random draw -- is compared element by

@@ -262,3 +262,51 @@ def test_outer_and_matvec(dtype, arr):
         assert_close("outer", Cg[c], O.outer(Ms[c], Vs[c], 4, 2), TOL[dtype]["fwd"])
         assert_close("matvec", P0g[c], O.band_matvec(As[c], 2, 3, 0, Vs[c]), TOL[dtype]["fwd"])
         assert_close("matvecT", P1g[c], O.band_matvec(As[c], 2, 3, 1, Vs[c]), TOL[dtype]["fwd"])
+
+
+# --------------------------------------------------------------------------- Alg. 5 (banded RHS)
+
+@pytest.mark.parametrize("arr", ARRANGEMENTS)
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("trans", [0, 1])
+def test_solve_band_and_vjp(dtype, trans, arr):
+    """banded_solve_band (Alg. 5) and its Table 1 adjoint against the oracle:
+    mixed bandwidths of L, a (2, 3) banded right-hand side, ragged n."""
+    from test_oracle_pins import rand_general
+    rlo, rup = 2, 3
+    olo, oup = (4, 3) if trans == 0 else (2, 5)
+    shapes = [(1, 2), (4, 3), (17, 5), (300, 1), (1000, 2), (1501, 3)]
+    rows = max(rlo + rup + 1, olo + oup + 1)
+    ins_l = max(l for _, l in shapes)
+    insts, lay, plan = setup(sorted(shapes, key=lambda s: (s[1], -s[0])), 1, dtype, TUNINGS["whole"],
+                             extra_rows=rows, arr=arr)
+    Ls = [rounded(O.cholesky(i.Q)[0], dtype) for i in insts]
+    Rs = [rounded(rand_general(i.n, rlo, rup, 70 + c), dtype) for c, i in enumerate(insts)]
+    Obs = [rounded(rand_general(i.n, olo, oup, 80 + c), dtype) for c, i in enumerate(insts)]
+    L, R, Ob = dev(lay, lay.pack_band(Ls)), dev(lay, lay.pack_band(Rs)), dev(lay, lay.pack_band(Obs))
+    Om, G = lay.band_pool(fill=3.0), lay.band_pool(fill=3.0)
+    Rb, Lb = lay.band_pool(fill=3.0), lay.band_pool(fill=0.0)
+    B.banded_solve_band(plan.handle, L, R, rlo, rup, Om, olo, oup, trans)
+    B.banded_solve_band_vjp(plan.handle, L, Om, olo, oup, Ob, trans, rlo, rup, G, Rb, Lb, 0)
+    sync()
+    Og = lay.unpack_band(Om, rows=olo + oup + 1)
+    Rbg = lay.unpack_band(Rb, rows=rlo + rup + 1)
+    Lbg = lay.unpack_band(Lb)
+    assert ins_l + 1 + rows >= rows
+    for c, i in enumerate(insts):
+        ref = O.solve_band(Ls[c], Rs[c], rlo, rup, trans, olo, oup)
+        assert_close("O", Og[c], ref, TOL[dtype]["fwd"])
+        rrb, rlb = O.solve_band_vjp(Ls[c], trans, ref, olo, oup, Obs[c], rlo, rup)
+        assert_close("Rbar", Rbg[c], rrb, TOL[dtype]["grad"])
+        assert_close("Lbar", Lbg[c], rlb, TOL[dtype]["grad"])
+
+
+def test_solve_band_rejects_inexact_bands():
+    shapes = [(10, 2)]
+    insts, lay, plan = setup(shapes, 1, B.BND_F64, TUNINGS["whole"], extra_rows=8)
+    x = lay.band_pool()
+    y, z = lay.band_pool(), lay.band_pool()
+    with pytest.raises(B.BandedError):
+        B.banded_solve_band(plan.handle, x, y, 1, 3, z, 2, 2, 0)      # oup < rup
+    with pytest.raises(B.BandedError):
+        B.banded_solve_band(plan.handle, x, y, 3, 1, z, 2, 2, 1)      # olo < rlo

@@ -662,3 +662,59 @@ def test_matern_kl_grad_at_tiny_gaps_matches_high_precision(oracle):
         for j in range(N - d):
             ref_gL[d, j] = float(G[j + d, j])
     assert rel(gL, ref_gL) < 1e-9
+
+
+# --------------------------------------------------------------------------- Alg. 5 (banded RHS)
+
+def _gdense(B, lo, up, n):
+    M = np.zeros((n, n))
+    for r in range(lo + up + 1):
+        k = r - up
+        for c in range(n):
+            if 0 <= c + k < n:
+                M[c + k, c] = B[r, c]
+    return M
+
+
+def _gband(M, lo, up):
+    n = M.shape[0]
+    B = np.zeros((lo + up + 1, n))
+    for r in range(lo + up + 1):
+        k = r - up
+        for c in range(n):
+            if 0 <= c + k < n:
+                B[r, c] = M[c + k, c]
+    return B
+
+
+@pytest.mark.parametrize("trans,olo,oup", [(0, 2, 3), (0, 5, 4), (1, 1, 4), (1, 3, 6)])
+@pytest.mark.parametrize("n,l", [(1, 2), (9, 2), (30, 4)])
+def test_solve_band_matches_dense(oracle, n, l, trans, olo, oup):
+    Q = spd(n, l, seed=61)
+    L, _ = oracle.cholesky(Q)
+    rlo, rup = 1, 3
+    R = _gband(_gdense(W.rng_for(62).normal(size=(rlo + rup + 1, n)), rlo, rup, n), rlo, rup)
+    O = oracle.solve_band(L, R, rlo, rup, trans, olo, oup)
+    Ld = W.dense_from_lower_band(L, False)
+    ref = np.linalg.solve(Ld.T if trans else Ld, _gdense(R, rlo, rup, n))
+    assert rel(O, _gband(ref, olo, oup)) < 1e-13
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_solve_band_vjp_matches_autograd(oracle, trans):
+    n, l = 14, 3
+    rlo, rup = 2, 2
+    olo, oup = (3, 2) if trans == 0 else (2, 4)
+    Q = spd(n, l, seed=63)
+    L, _ = oracle.cholesky(Q)
+    rng = W.rng_for(64)
+    R = _gband(_gdense(rng.normal(size=(rlo + rup + 1, n)), rlo, rup, n), rlo, rup)
+    O = oracle.solve_band(L, R, rlo, rup, trans, olo, oup)
+    Obar = _gband(_gdense(rng.normal(size=(olo + oup + 1, n)), olo, oup, n), olo, oup)
+    Rbar, Lbar = oracle.solve_band_vjp(L, trans, O, olo, oup, Obar, rlo, rup)
+    Lt = torch.tensor(W.dense_from_lower_band(L, False), requires_grad=True)
+    Rt = torch.tensor(_gdense(R, rlo, rup, n), requires_grad=True)
+    Od = torch.linalg.solve_triangular(Lt.T if trans else Lt, Rt, upper=bool(trans))
+    (Od * torch.tensor(_gdense(Obar, olo, oup, n))).sum().backward()
+    assert rel(Rbar, _gband(Rt.grad.numpy(), rlo, rup)) < 1e-12
+    assert rel(Lbar, W.lower_band_from_dense(Lt.grad.numpy(), l)) < 1e-12
