@@ -304,3 +304,69 @@ def _zero_corners(band):
     for d in range(1, band.shape[0]):
         band[d, max(n - d, 0):] = 0.0
     return band
+
+
+# ---------------------------------------------------------------------------
+# Inference compositions of Sec. 3 (marginal likelihood with partial
+# observations, whitened log joint for HMC, state-space GP regression through
+# natural parameters), from the oracle's operators.
+# ---------------------------------------------------------------------------
+
+def marginal_likelihood(Q, obs, y, tau2, logdet_prior=None):
+    """log p(y | theta) for f ~ N(0, Q^{-1}) (lower band storage) observed at the
+    node indices `obs` with Gaussian noise tau2 (Sec. 3.1, marginal-likelihood
+    equation with E the 0/1 selection of the observed nodes):
+      -n/2 log 2 pi - log|L| + log|L_Q| - n/2 log tau2 - y^T y / (2 tau2)
+      + |L^{-1} E^T y|^2 / (2 tau2^2),   L L^T = Q + E^T E / tau2,  L_Q L_Q^T = Q.
+    `logdet_prior` replaces 2 log|L_Q| when the prior precision comes factored."""
+    Q = np.asarray(Q, dtype=np.float64)
+    obs = np.asarray(obs, dtype=np.int64)
+    y = np.asarray(y, dtype=np.float64)
+    n = obs.shape[0]
+    Qpost = Q.copy()
+    Qpost[0, obs] += 1.0 / tau2
+    L, info = cholesky(Qpost)
+    if info:
+        raise ValueError("posterior precision not SPD")
+    if logdet_prior is None:
+        LQ, info = cholesky(Q)
+        if info:
+            raise ValueError("prior precision not SPD")
+        logdet_prior = logdet(LQ)
+    ey = np.zeros(Q.shape[1])
+    ey[obs] = y
+    R = solve(L, ey, 0)
+    return (-0.5 * n * math.log(2 * math.pi) - 0.5 * logdet(L) + 0.5 * logdet_prior - 0.5 * n * math.log(tau2)
+            - float(y @ y) / (2 * tau2) + float(R @ R) / (2 * tau2 * tau2))
+
+
+def whitened_log_joint(Q, v, obs, y, tau2):
+    """log p(v) + sum_i log N(y_i; F_i, tau2) with F = L_Q^{-T} v (Sec. 3.2 and the
+    log-likelihood pseudocode for HMC; the parameter prior log p(theta) is the
+    caller's)."""
+    L, info = cholesky(Q)
+    if info:
+        raise ValueError("precision not SPD")
+    v = np.asarray(v, dtype=np.float64)
+    F = solve(L, v, 1)
+    obs = np.asarray(obs, dtype=np.int64)
+    r = np.asarray(y, dtype=np.float64) - F[obs]
+    N = v.shape[0]
+    return (-0.5 * N * math.log(2 * math.pi) - 0.5 * float(v @ v)
+            - 0.5 * obs.shape[0] * math.log(2 * math.pi * tau2) - float(r @ r) / (2 * tau2))
+
+
+def ssm_gpr_log_marginal(t, ell, s2, y, tau2):
+    """log p(y) of GP regression with a Matern-3/2 kernel through its state-space
+    form (App. C, GP regression with banded matrices): the states (f, f') of
+    the inputs t have prior precision Q_p = M^T M; y observes every f with
+    noise tau2.  Natural parameters: Lambda_post = Q_p + H^T H / tau2,
+    eta_post = H^T y / tau2 (zero prior mean), and
+      log p(y) = -T/2 log(2 pi tau2) - y^T y / (2 tau2) + 1/2 log|Q_p|
+                 - 1/2 log|Lambda_post| + 1/2 |C_post^{-1} eta_post|^2,
+    the same expression as marginal_likelihood with E selecting the f states
+    (log|Q_p| = 2 sum log|M_ii| from the factor)."""
+    M = matern_M_band(np.asarray(t, dtype=np.float64), ell, s2)
+    Qp = product(M, 3, 0, 1, M, 3, 0, 0, 3, 0)
+    obs = 2 * np.arange(len(t))
+    return marginal_likelihood(Qp, obs, y, tau2, logdet_prior=2.0 * float(np.sum(np.log(np.abs(M[0])))))

@@ -185,5 +185,49 @@ def matvec(plan, A, a_band, transA, V):
     return Matvec.apply(plan, A, tuple(a_band), int(transA), V)
 
 
-def gmm_step(plan, Q, Bm):
+class GMMStepRecompute(torch.autograd.Function):
+    """GMMStep that keeps no Cholesky factor between the forward and the backward:
+    the forward writes L to a temporary that it drops, and the backward
+    recomputes L from Q (one Cholesky sweep) before the fused backward kernels.
+    What autograd holds per batch is Q, X and S instead of L, X and S plus the
+    caller's Q -- one band pool less, for batches that are processed in chunks
+    because their saved tensors would not fit in HBM.  Results are bitwise those
+    of GMMStep (the same kernels recompute the same L)."""
+
+    @staticmethod
+    def forward(ctx, plan, Q, Bm):
+        lay = plan.layout
+        L, S, X = torch.zeros_like(Q), torch.zeros_like(Q), torch.zeros_like(Bm)
+        logdet = torch.empty(lay.count, dtype=torch.float64, device=Q.device)
+        info = torch.empty(lay.count, dtype=torch.int32, device=Q.device)
+        Qc = Q.contiguous()
+        B.banded_gmm_forward(plan.handle, Qc, Bm.contiguous(), L, X, S, logdet, info)
+        del L
+        ctx.plan = plan
+        ctx.save_for_backward(Qc, X, S)
+        ctx.mark_non_differentiable(info)
+        return X, S, logdet, info
+
+    @staticmethod
+    def backward(ctx, Xbar, Sbar, ldbar, _info):
+        Q, X, S = ctx.saved_tensors
+        lay = ctx.plan.layout
+        L = torch.zeros_like(Q)
+        logdet = torch.empty(lay.count, dtype=torch.float64, device=Q.device)
+        info = torch.empty(lay.count, dtype=torch.int32, device=Q.device)
+        B.banded_cholesky(ctx.plan.handle, Q, L, logdet, info)
+        Xbar = _zeros_like_or(Xbar, X)
+        Sbar = _zeros_like_or(Sbar, S)
+        ldbar = None if ldbar is None else ldbar.contiguous().to(torch.float64)
+        Qbar, Bbar = torch.zeros_like(L), torch.zeros_like(X)
+        B.banded_gmm_backward(ctx.plan.handle, L, X, S, Xbar, Sbar, ldbar, Qbar, Bbar)
+        return None, Qbar, Bbar
+
+
+def gmm_step(plan, Q, Bm, recompute_L=False):
+    """(X, S, logdet, L, info) of the fused step; with recompute_L the factor is
+    not kept for the backward (L is returned as None) and is recomputed there."""
+    if recompute_L:
+        X, S, logdet, info = GMMStepRecompute.apply(plan, Q, Bm)
+        return X, S, logdet, None, info
     return GMMStep.apply(plan, Q, Bm)

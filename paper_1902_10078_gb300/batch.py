@@ -215,16 +215,29 @@ def _cuda_timer(fn, reps, warmup):
     return a.elapsed_time(b) / reps
 
 
-def autotune(layout, make_step, candidates=(256, 320, 384, 512, 768, 1024, 2048), reps=3, warmup=2,
-             use_cache=True, plan_factory=None, timer=None):
-    """Choose the segment length of a batch by timing one step per candidate.
+# Default candidates: segment length x warm-up slope (rows per unit of bandwidth,
+# plus 32), and the direct kernels at the library defaults.
+DEFAULT_CANDIDATES = tuple(
+    [dict(seg_len=s, warm_per_l=w, warm_base=32) for s in (256, 384, 512, 768) for w in (12, 16, 24)]
+    + [dict(flags=1)])
 
-    `make_step(plan)` returns a callable that runs one step of the caller's
-    workload on `plan`.  Each candidate gets its own plan; the fastest
-    segment length is returned as a tuning dict (with the timings) and stored
-    in a JSON cache keyed by `workload_signature` (path: $BND_AUTOTUNE_CACHE,
-    default ~/.cache/paper_1902_10078_gb300/autotune.json), which later calls
-    consult first.  `plan_factory` and `timer` replace Plan construction and
+
+def _candidate_key(c):
+    return ",".join(f"{k}={c[k]}" for k in sorted(c))
+
+
+def autotune(layout, make_step, candidates=DEFAULT_CANDIDATES, reps=3, warmup=2, use_cache=True,
+             plan_factory=None, timer=None):
+    """Choose the schedule of a batch by timing one step per candidate.
+
+    A candidate is a tuning dict (segment length, warm-up slope, flags: staged
+    or direct kernels) or a bare segment length.  `make_step(plan)` returns a
+    callable that runs one step of the caller's workload on `plan`.  Each
+    candidate gets its own plan; the fastest tuning is returned (with the
+    timings by candidate) and stored in a JSON cache keyed by
+    `workload_signature` (path: $BND_AUTOTUNE_CACHE, default
+    ~/.cache/paper_1902_10078_gb300/autotune.json), which later calls consult
+    first.  `plan_factory` and `timer` replace Plan construction and
     CUDA-event timing (tests)."""
     import json
     import os
@@ -238,22 +251,25 @@ def autotune(layout, make_step, candidates=(256, 320, 384, 512, 768, 1024, 2048)
         except (OSError, ValueError):
             cache = {}
         if key in cache:
-            return dict(seg_len=int(cache[key]["seg_len"])), cache[key].get("timings", {})
+            return dict(cache[key]["tuning"]), cache[key].get("timings", {})
     plan_factory = plan_factory or (lambda tuning: Plan(layout, tuning))
     timer = timer or _cuda_timer
-    timings = {}
-    for seg in candidates:
-        plan = plan_factory(dict(seg_len=int(seg)))
+    timings, by_key = {}, {}
+    for cand in candidates:
+        tuning = dict(seg_len=int(cand)) if not isinstance(cand, dict) else dict(cand)
+        k = _candidate_key(tuning)
+        plan = plan_factory(tuning)
         try:
-            timings[str(seg)] = float(timer(make_step(plan), reps, warmup))
+            timings[k] = float(timer(make_step(plan), reps, warmup))
+            by_key[k] = tuning
         finally:
             close = getattr(plan, "close", None)
             if close:
                 close()
     best = min(timings, key=timings.get)
     if use_cache:
-        cache[key] = {"seg_len": int(best), "timings": timings}
+        cache[key] = {"tuning": by_key[best], "timings": timings}
         os.makedirs(os.path.dirname(path), exist_ok=True)
         with open(path, "w") as f:
             json.dump(cache, f, indent=1)
-    return dict(seg_len=int(best)), timings
+    return dict(by_key[best]), timings

@@ -29,13 +29,14 @@ def symmetric_weights(layout, device="cuda"):
     return w.to(device=device)
 
 
-def chain_loss(plan, Q, b, W, wsym):
+def chain_loss(plan, Q, b, W, wsym, recompute_L=False):
     """-1/2 b^T Q^{-1} b + 1/2 log det Q + 1/2 tr(band(Q^{-1}) W), summed over instances.
 
     Q, W: band pools (W symmetric with the bandwidth of Q); b: RHS pool (k = 1);
     wsym: symmetric_weights(layout).  Differentiable in Q (and b) through the
-    fused GMM step kernels."""
-    X, S, logdet, _L, info = AG.gmm_step(plan, Q, b)
+    fused GMM step kernels; recompute_L keeps no Cholesky factor for the
+    backward (it is recomputed from Q there)."""
+    X, S, logdet, _L, info = AG.gmm_step(plan, Q, b, recompute_L=recompute_L)
     quad = (b.to(torch.float64) * X.to(torch.float64)).sum()
     trace = (wsym * S.to(torch.float64) * W.to(torch.float64)).sum()
     return -0.5 * quad + 0.5 * logdet.sum() + 0.5 * trace, info

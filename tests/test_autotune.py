@@ -29,13 +29,30 @@ def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
     tuning, timings = BT.autotune(lay, lambda plan: plan.tuning["seg_len"], candidates=(256, 384, 512),
                                   plan_factory=factory, timer=lambda seg, reps, warmup: cost[seg])
     assert tuning == {"seg_len": 384}
-    assert timings == {"256": 3.0, "384": 1.5, "512": 2.0}
+    assert timings == {"seg_len=256": 3.0, "seg_len=384": 1.5, "seg_len=512": 2.0}
     assert all(p.closed for p in made) and len(made) == 3
     stored = json.load(open(tmp_path / "tune.json"))
-    assert stored[BT.workload_signature(lay)]["seg_len"] == 384
+    assert stored[BT.workload_signature(lay)]["tuning"] == {"seg_len": 384}
     # a second call is answered from the cache without building plans
     tuning2, _ = BT.autotune(lay, lambda plan: None, plan_factory=lambda t: 1 / 0, timer=None)
     assert tuning2 == {"seg_len": 384}
+
+
+def test_autotune_searches_segments_warmups_and_kernels(tmp_path, monkeypatch):
+    """The default candidates cover segment length x warm-up slope and the
+    direct kernels; the fastest dict is returned whole."""
+    monkeypatch.setenv("BND_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    lay = BT.Layout([5000, 6000, 300], [3, 3, 7], 4, B.BND_F32, panels=True)
+
+    def cost(tuning):
+        if tuning.get("flags"):
+            return 9.0
+        return abs(tuning["seg_len"] - 512) / 100 + abs(tuning["warm_per_l"] - 16)
+
+    tuning, timings = BT.autotune(lay, lambda plan: plan.tuning, plan_factory=FakePlan,
+                                  timer=lambda t, reps, warmup: cost(t))
+    assert tuning == {"seg_len": 512, "warm_per_l": 16, "warm_base": 32}
+    assert len(timings) == len(BT.DEFAULT_CANDIDATES) == 13
 
 
 def test_signature_separates_workloads():

@@ -54,3 +54,20 @@ def test_summarize_ncu_sums_dram_bytes(tmp_path, monkeypatch):
     t = json.loads(out.read_text())
     assert t["dram_bytes_per_call"] == 1.5e6 + 5e5 + 1000
     assert t["launches"] == 2 and t["band_entries"] == 123 and t["source_hash"] == bench.source_hash()
+
+
+def test_strong_scaling_layouts_cover_the_batch_once():
+    """bench.py --scaling strong: the ranks' layouts hold every instance of the one
+    batch exactly once, each with the shape and seed it has in the whole batch."""
+    import bench
+    from paper_1902_10078_gb300 import workloads as W
+    count = 200
+    ns, ls = W.batched_shapes(count, seed=W.BASE_SEED, ls=(1, 2, 3, 5, 7))
+    seen = []
+    for rank in range(2):
+        lay, seeds, order = bench.batch_layout(count, 4, (1, 2, 3, 5, 7), True, rank, 2, True)
+        for p, i in enumerate(order):
+            assert (lay.ns[p], lay.ls[p]) == (int(ns[i]), int(ls[i]))
+            assert seeds[p] == W.BASE_SEED + i
+        seen += order
+    assert sorted(seen) == list(range(count))

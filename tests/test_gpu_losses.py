@@ -158,3 +158,30 @@ def test_matern_kl_full_size(dtype):
     assert abs(float(kl.detach()) - ref) <= tol * max(1.0, abs(ref)), (float(kl.detach()), ref)
     # gradients of a slice of the batch (first, middle, last panel groups) against the oracle adjoint
     check_kl_gradients(procs, dtype, lay, Lq, m, ells, [0, 31, 32, 128, 255], tol_g)
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_recomputed_factor_gives_identical_gradients(dtype):
+    """The loss with the Cholesky factor recomputed in the backward (nothing but Q,
+    X and S kept between the passes) gives bitwise the same value and gradient
+    as the loss that keeps L, on a segmented mixed batch."""
+    shapes = [(20000, 3), (5000, 1), (777, 7), (12000, 5)]
+    lay = BT.Layout([s[0] for s in shapes], [s[1] for s in shapes], 1, dtype, panels=True)
+    plan = BT.Plan(lay)
+    rng = W.rng_for(606)
+    Qs = [rounded(W.spd_band(W.rng_for(607 + i), n, l), dtype) for i, (n, l) in enumerate(shapes)]
+    bs = [rounded(rng.normal(size=(1, n)), dtype) for n, _ in shapes]
+    Ws = [rounded(W.symmetric_band_weights(rng, n, l), dtype) for n, l in shapes]
+    wsym = LS.symmetric_weights(lay)
+    grads, vals = [], []
+    for rec in (False, True):
+        Qd = torch.tensor(lay.pack_band(Qs), device="cuda", requires_grad=True)
+        bd = torch.tensor(lay.pack_rhs(bs), device="cuda")
+        Wd = torch.tensor(lay.pack_band(Ws), device="cuda")
+        loss, info = LS.chain_loss(plan, Qd, bd, Wd, wsym, recompute_L=rec)
+        loss.backward()
+        assert int(info.abs().sum()) == 0
+        vals.append(float(loss.detach()))
+        grads.append(Qd.grad.detach().clone())
+    assert vals[0] == vals[1]
+    assert torch.equal(grads[0], grads[1])

@@ -243,3 +243,31 @@ def test_wide_bands_sixteen_rhs(dtype):
         assert_close("Qbar", Qg[c], r["Qbar"], tol["grad"])
         assert_close("Bbar", Bg[c], r["Bbar"], tol["grad"])
         assert abs(got["logdet"][c] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))
+
+
+@pytest.mark.parametrize("dtype", [B.BND_F64, B.BND_F32])
+def test_graph_gmrf_reordered(dtype):
+    """A random-geometric-graph GMRF (kappa^2 I + Laplacian, 2000 nodes) reordered
+    by reverse Cuthill-McKee to bandwidth 85: the fused step on the wide-band
+    kernels against the oracle."""
+    from paper_1902_10078_gb300 import workloads as W
+    from gpu_helpers import rounded
+    from paper_1902_10078_gb300 import batch as BT
+    Qg, l, _, _ = W.gmrf_graph(2000)
+    n = Qg.shape[1]
+    ins = W.make_instance(n, l, 4, 2024)
+    ins.Q = rounded(Qg, dtype)
+    for key in ("B", "Xbar", "Sbar"):
+        setattr(ins, key, rounded(getattr(ins, key), dtype))
+    lay = BT.Layout([n], [l], 4, dtype)
+    plan = BT.Plan(lay)
+    got = run_gmm(lay, plan, [ins])
+    r = O.batch_step([ins])[0][0]
+    tol = TOL[dtype]
+    assert got["info"][0] == 0
+    assert_close("L", lay.unpack_band(got["L"])[0], r["L"], tol["fwd"])
+    assert_close("S", lay.unpack_band(got["S"])[0], r["S"], tol["fwd"])
+    assert_close("X", lay.unpack_rhs(got["X"])[0], r["X"], tol["fwd"])
+    assert_close("Qbar", lay.unpack_band(got["Qb"])[0], r["Qbar"], tol["grad"])
+    assert_close("Bbar", lay.unpack_rhs(got["Bb"])[0], r["Bbar"], tol["grad"])
+    assert abs(got["logdet"][0] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))

@@ -68,3 +68,25 @@ def test_layout_insts_describe_the_pools(panels):
     for d in lay.insts():
         assert d["cs"] == (32 if panels else 1)
         assert d["ld"] >= d["n"] * d["cs"] and d["ldr"] >= d["n"] * d["cs"]
+
+
+def test_gmrf_graph_is_banded_spd_laplacian():
+    """The synthetic graph GMRF: after the reverse Cuthill-McKee reordering every
+    edge lies inside the returned band, the diagonal is kappa^2 + degree, and the
+    precision is SPD (dense eigenvalues at small N)."""
+    import numpy as np
+    from paper_1902_10078_gb300 import workloads as W
+    N = 300
+    Q, l, perm, edges = W.gmrf_graph(N, seed=5)
+    assert Q.shape == (l + 1, N)
+    assert sorted(perm.tolist()) == list(range(N))
+    inv = np.empty(N, dtype=int)
+    inv[perm] = np.arange(N)
+    D = W.dense_from_lower_band(Q, True)
+    for a, b in edges:
+        i, j = inv[a], inv[b]
+        assert abs(i - j) <= l and D[i, j] == -1.0
+    assert np.count_nonzero(np.tril(D, -1)) == len(edges)
+    assert np.allclose(np.diag(D) - 0.1, -(D - np.diag(np.diag(D))).sum(axis=1))
+    assert np.linalg.eigvalsh(D).min() > 0.0
+    assert l < N // 4                          # the reordering made it narrow

@@ -718,3 +718,53 @@ def test_solve_band_vjp_matches_autograd(oracle, trans):
     (Od * torch.tensor(_gdense(Obar, olo, oup, n))).sum().backward()
     assert rel(Rbar, _gband(Rt.grad.numpy(), rlo, rup)) < 1e-12
     assert rel(Lbar, W.lower_band_from_dense(Lt.grad.numpy(), l)) < 1e-12
+
+
+# --------------------------------------------------------------------------- Sec. 3 inference compositions
+
+def test_marginal_likelihood_matches_dense_gaussian(oracle):
+    from oracle.losses import marginal_likelihood
+    n, l = 40, 3
+    Q = spd(n, l, seed=71)
+    rng = W.rng_for(72)
+    obs = np.sort(rng.choice(n, size=15, replace=False))
+    y = rng.normal(size=15)
+    tau2 = 0.3
+    got = marginal_likelihood(Q, obs, y, tau2)
+    K = np.linalg.inv(W.dense_from_lower_band(Q, True))[np.ix_(obs, obs)] + tau2 * np.eye(15)
+    ref = -0.5 * (15 * math.log(2 * math.pi) + np.linalg.slogdet(K)[1] + y @ np.linalg.solve(K, y))
+    assert abs(got - ref) < 1e-10 * abs(ref)
+
+
+def test_whitened_log_joint_matches_dense(oracle):
+    from oracle.losses import whitened_log_joint
+    n, l = 30, 2
+    Q = spd(n, l, seed=73)
+    rng = W.rng_for(74)
+    v = rng.normal(size=n)
+    obs = np.array([0, 3, 7, 8, 20, 29])
+    y = rng.normal(size=obs.shape[0])
+    tau2 = 0.5
+    got = whitened_log_joint(Q, v, obs, y, tau2)
+    Ld = np.linalg.cholesky(W.dense_from_lower_band(Q, True))
+    F = np.linalg.solve(Ld.T, v)                 # F ~ N(0, Q^{-1}) when v ~ N(0, I)
+    ref = (-0.5 * n * math.log(2 * math.pi) - 0.5 * v @ v
+           + sum(-0.5 * math.log(2 * math.pi * tau2) - (y[i] - F[o]) ** 2 / (2 * tau2) for i, o in enumerate(obs)))
+    assert abs(got - ref) < 1e-11 * abs(ref)
+
+
+def test_ssm_gpr_matches_kernel_regression(oracle):
+    """The state-space marginal likelihood equals the dense GP marginal likelihood
+    with the Matern-3/2 kernel matrix of the inputs (an independent route)."""
+    from oracle.losses import ssm_gpr_log_marginal
+    rng = W.rng_for(75)
+    n = 25
+    t = np.concatenate([[0.0], np.cumsum(rng.exponential(1.0, n - 1) + 0.01)])
+    ell, s2, tau2 = 1.3, 0.8, 0.2
+    y = rng.normal(size=n)
+    got = ssm_gpr_log_marginal(t, ell, s2, y, tau2)
+    lam = math.sqrt(3.0) / ell
+    a = np.abs(t[:, None] - t[None, :])
+    K = s2 * (1 + lam * a) * np.exp(-lam * a) + tau2 * np.eye(n)
+    ref = -0.5 * (n * math.log(2 * math.pi) + np.linalg.slogdet(K)[1] + y @ np.linalg.solve(K, y))
+    assert abs(got - ref) < 1e-9 * abs(ref)
