@@ -45,19 +45,35 @@ WORKLOAD = "uneven batch: 4096 instances, n log-uniform [1000, 65536], l in {1,2
 
 # --------------------------------------------------------------------------- inputs
 
-def batch_layout(count, k, ls, panels, rank=0):
-    """The uneven batch of `rank`: its pool layout and every slot's seed.
+def batch_layout(count, k, ls, panels, rank=0, world=1, strong=False):
+    """The uneven batch of `rank`: its pool layout, every slot's seed and the
+    original index of every slot.
 
-    Instance i (original order) has the i-th drawn shape and seed
-    BASE_SEED + rank * count + i; a panel layout reorders the instances
-    (panel_order) and carries each one's seed along, so slot p holds original
-    instance order[p] whatever the arrangement."""
+    Weak scaling (default): every rank draws its own batch of `count`
+    instances; instance i (original order) has the i-th drawn shape and seed
+    BASE_SEED + rank * count + i.  Strong scaling: one batch of `count`
+    instances (rank 0's draw) is split over the ranks by shard.partition
+    (longest-processing-time on n (l+1)^2), each rank keeping its share with
+    the shapes and seeds the instances have in the whole batch.  A panel
+    layout reorders the rank's instances (panel_order) and carries each one's
+    seed along, so slot p holds original instance order[p] whatever the
+    arrangement."""
     from paper_1902_10078_gb300 import batch as BT
     from paper_1902_10078_gb300 import binding as B
-    ns, lss = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919, ls=ls)
-    order = BT.panel_order(ns, lss) if panels else list(range(count))
+    from paper_1902_10078_gb300 import shard
+    if strong:
+        ns, lss = W.batched_shapes(count, seed=W.BASE_SEED, ls=ls)
+        mine = shard.partition([int(x) for x in ns], [int(x) for x in lss], world)[rank]
+        seed0 = W.BASE_SEED
+    else:
+        ns, lss = W.batched_shapes(count, seed=W.BASE_SEED + rank * 7919, ls=ls)
+        mine = list(range(count))
+        seed0 = W.BASE_SEED + rank * count
+    sub_ns, sub_ls = [int(ns[i]) for i in mine], [int(lss[i]) for i in mine]
+    local = BT.panel_order(sub_ns, sub_ls) if panels else list(range(len(mine)))
+    order = [int(mine[q]) for q in local]
     lay = BT.Layout([int(ns[i]) for i in order], [int(lss[i]) for i in order], k, B.BND_F32, panels=panels)
-    seeds = [W.BASE_SEED + rank * count + int(i) for i in order]
+    seeds = [seed0 + i for i in order]
     return lay, seeds, order
 
 
@@ -202,6 +218,17 @@ def max_over_ranks(values, world, device):
     return [float(x) for x in t.tolist()]
 
 
+def sum_over_ranks(value, world, device):
+    """Sum of a per-rank count over the ranks (every rank gets the result)."""
+    import torch
+    if world <= 1:
+        return float(value)
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -219,7 +246,10 @@ def run_ours(args, rank, world, device_index):
 
     count = args.count
     panels = args.layout == "panels"
-    lay, seeds, order = batch_layout(count, args.k, tuple(int(x) for x in args.ls.split(",")), panels, rank)
+    strong = args.scaling == "strong"
+    lay, seeds, order = batch_layout(count, args.k, tuple(int(x) for x in args.ls.split(",")), panels, rank,
+                                     world, strong)
+    count = lay.count                      # this rank's instances
     host = W.fill_pools(lay, seeds, args.workers)
     torch.cuda.set_device(device_index)
     from paper_1902_10078_gb300 import build as bld
@@ -241,8 +271,8 @@ def run_ours(args, rank, world, device_index):
                 B.banded_gmm_backward(pl.handle, L, X, S, dev["Xbar"], dev["Sbar"], ldbar, Qb, Bb)
             return one
         best, timings = BT.autotune(lay, make_step, use_cache=False)
-        tuning["seg_len"] = best["seg_len"]
-        autotuned = {"seg_len": best["seg_len"], "ms_per_candidate": timings}
+        tuning.update(best)
+        autotuned = {"chosen": best, "ms_per_candidate": timings}
     plan = BT.Plan(lay, tuning)
     expect = B.LAYOUT_PANELS if panels else B.LAYOUT_ROWS
     assert B.bnd_plan_layout(plan.handle) == expect, "the plan did not take the intended arrangement"
@@ -344,7 +374,9 @@ def run_ours(args, rank, world, device_index):
     if rank == 0 and not args.no_cpu_baseline:
         slot_of = {int(o): p for p, o in enumerate(order)}
         sample_out = {}
-        for i in cpu_sample(count, args.cpu_sample):
+        for i in cpu_sample(args.count, args.cpu_sample):
+            if int(i) not in slot_of:      # strong scaling: held by another rank
+                continue
             p = slot_of[int(i)]
             sample_out[int(i)] = dict(
                 L=lay.band_view(L, p).cpu().numpy(), S=lay.band_view(S, p).cpu().numpy(),
@@ -353,6 +385,7 @@ def run_ours(args, rank, world, device_index):
 
     entries = int(sum(n * (l + 1) for n, l in zip(lay.ns, lay.ls)))
     ms, ms_e2e, ms_fwd, ms_bwd = max_over_ranks([ms, ms_e2e, ms_fwd, ms_bwd], world, "cuda")
+    entries_all = sum_over_ranks(entries, world, "cuda")
 
     plain = None
     if args.plain and rank == 0:
@@ -363,6 +396,7 @@ def run_ours(args, rank, world, device_index):
     launches_per_step = 4 * (classes + (1 if plan.chains > count else 0))
     fwd_b, bwd_b, floor_b = algorithmic_bytes(lay)
     return dict(lay=lay, plan=plan, ms=ms, ms_e2e=ms_e2e, ms_fwd=ms_fwd, ms_bwd=ms_bwd, entries=entries,
+                entries_all=entries_all,
                 autotuned=autotuned,
                 fwd_bytes=fwd_b, bwd_bytes=bwd_b, floor_bytes=floor_b, clocks=clk, h2d=h2d, d2h=d2h,
                 fixups=fixups, plain=plain, launches=launches_per_step * args.steps, sample_out=sample_out)
@@ -445,6 +479,8 @@ def cpu_baseline(args, sample_count=None, gpu_out=None):
         worst = {k: 0.0 for k in PARITY_TOL}
         bad = 0
         for i, r in zip(idx, res):
+            if int(i) not in gpu_out:       # strong scaling: held by another rank
+                continue
             g = gpu_out[int(i)]
             bad += int(g["info"] != 0 or r["info"] != 0)
             for key in ("L", "S", "Qbar"):
@@ -452,7 +488,7 @@ def cpu_baseline(args, sample_count=None, gpu_out=None):
             for key in ("X", "Bbar"):
                 worst[key] = max(worst[key], _normwise(g[key], r[key]))
             worst["logdet"] = max(worst["logdet"], abs(g["logdet"] - r["logdet"]) / max(1.0, abs(r["logdet"])))
-        parity = {"instances": len(insts), "max_normwise_err": worst, "tol": PARITY_TOL, "non_spd": bad,
+        parity = {"instances": sum(int(int(i) in gpu_out) for i in idx), "max_normwise_err": worst, "tol": PARITY_TOL, "non_spd": bad,
                   "pass": bad == 0 and all(worst[k] <= PARITY_TOL[k] for k in worst)}
     return cb, dt, parity
 
@@ -569,22 +605,27 @@ def run_config(args):
             for name in args.wide_dtypes:
                 dt = dts[name]
                 n, k = 200_000, 16
-                lay, plan, step, info = gmm_setup([(n, l)], k, dt)
+                tuning = {key: v for key, v in (("seg_len", args.seg_len), ("warm_per_l", args.warm_per_l),
+                                                 ("warm_base", args.warm_base)) if v}
+                lay, plan, step, info = gmm_setup([(n, l)], k, dt, tuning or None)
                 step()
                 torch.cuda.synchronize()
-                ms = timed(step, 3)
+                ms = timed(step, 10)
+                fixups = [B.bnd_plan_fixups(plan.handle, kk) for kk in range(6)]
                 flops = 9.0 * n * l * l
                 pk = peaks.get("fp64_fma_tflops" if name == "f64" else "fp32_fma_tflops")
                 gf = flops / (ms * 1e-3) / 1e9
                 lines.append({"config": f"wide band n={n}, l={l}, k={k}, {name}: Cholesky, Q^-1 B, subset inverse "
                               "and their adjoints (fused forward + backward)", "ms_per_step": ms,
-                              "gflops_per_s": gf, "flops_per_step": flops, "info": int(info[0].item()),
+                              "segments": plan.chains, "segment_fixups_last_step_by_sweep_kind": fixups,
+                              "tuning": tuning, "gflops_per_s": gf, "flops_per_step": flops,
+                              "info": int(info[0].item()),
                               "roofline": {"bound": "fp64" if name == "f64" else "fp32", "achieved_tflops": gf / 1e3,
                                            "peak_tflops": pk, "frac": (gf / 1e3) / pk if pk else None,
                                            "peak_source": "measured (microbench/peaks.cu)"},
-                              "path": "one thread block per chain, computed window in shared memory, "
-                                      "O(l^2) row work spread over 512 threads; segments "
-                                      f"{plan.chains}"})
+                              "path": "one thread block per segment, computed window in shared memory, "
+                                      "O(l^2) row work spread over 512 threads; segment starts accepted "
+                                      "within the state's rounding noise"})
     elif args.config == 4:
         count, n = 256, 50_000
         procs = W.matern_batch(count, n)
@@ -615,6 +656,42 @@ def run_config(args):
                           "band_entries_per_s": count * 2 * n * 4 / (ms * 1e-3),
                           "note": "includes the FP64 torch construction of the prior factor M (flat over all "
                                   "processes) and its backward, timed alone in ms_prior_construction_fwd_bwd"})
+    elif args.config == 5:
+        # graph GMRF of the spatial workload's size: 11284 nodes, reverse Cuthill-McKee band
+        Qg, l, _, _ = W.gmrf_graph(11284)
+        n = Qg.shape[1]
+        ins = W.make_instance(n, l, 1, W.BASE_SEED)
+        ins.Q = Qg
+        for name in args.wide_dtypes:
+            dt = dts[name]
+            tuning = {key: v for key, v in (("seg_len", args.seg_len), ("warm_per_l", args.warm_per_l),
+                                             ("warm_base", args.warm_base)) if v}
+            lay = BT.Layout([n], [l], 1, dt)
+            plan = BT.Plan(lay, tuning or None)
+            dev = {key: torch.from_numpy(pool).cuda() for key, pool in (
+                ("Q", lay.pack_band([ins.Q])), ("Sbar", lay.pack_band([ins.Sbar])),
+                ("B", lay.pack_rhs([ins.B])), ("Xbar", lay.pack_rhs([ins.Xbar])))}
+            L, S, Qb = lay.band_pool(), lay.band_pool(), lay.band_pool()
+            X, Bb = lay.rhs_pool(), lay.rhs_pool()
+            ld = torch.empty(1, dtype=torch.float64, device="cuda")
+            info = torch.empty(1, dtype=torch.int32, device="cuda")
+            ldb = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+
+            def step():
+                B.banded_gmm_forward(plan.handle, dev["Q"], dev["B"], L, X, S, ld, info)
+                B.banded_gmm_backward(plan.handle, L, X, S, dev["Xbar"], dev["Sbar"], ldb, Qb, Bb)
+            ms = timed(step, 5)
+            fixups = [B.bnd_plan_fixups(plan.handle, kk) for kk in range(6)]
+            flops = 9.0 * n * l * l
+            pk = peaks.get("fp64_fma_tflops" if name == "f64" else "fp32_fma_tflops")
+            gf = flops / (ms * 1e-3) / 1e9
+            lines.append({"config": f"graph GMRF, {n} nodes (random geometric graph, kappa^2 I + Laplacian), "
+                          f"reverse Cuthill-McKee band l={l}, 1 RHS, {name}: fused forward + backward",
+                          "ms_per_step": ms, "segments": plan.chains,
+                          "segment_fixups_last_step_by_sweep_kind": fixups, "tuning": tuning,
+                          "gflops_per_s": gf, "info": int(info[0].item()),
+                          "roofline": {"bound": "fp64" if name == "f64" else "fp32", "achieved_tflops": gf / 1e3,
+                                       "peak_tflops": pk, "frac": (gf / 1e3) / pk if pk else None}})
     for line in lines:
         print(json.dumps(line), flush=True)
 
@@ -624,6 +701,8 @@ def run_config(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: a batch of --count instances per GPU; strong: one batch split over the GPUs")
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -644,7 +723,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="choose the segment length by timing candidates on this batch first")
-    ap.add_argument("--config", type=int, default=None, choices=[0, 1, 3, 4],
+    ap.add_argument("--config", type=int, default=None, choices=[0, 1, 3, 4, 5],
                     help="time another workload configuration instead of the uneven batch")
     ap.add_argument("--wide-ls", type=int, nargs="+", default=[64, 128], help="bandwidths of --config 3")
     ap.add_argument("--wide-dtypes", nargs="+", default=["f32", "f64"], help="dtypes of --config 3")
@@ -694,7 +773,8 @@ def main():
         return
     peaks, peak_kind = measured_peaks()
     lay = r["lay"]
-    entries_all = r["entries"] * world
+    entries_all = r["entries_all"]
+    scaling = args.scaling
     value = entries_all / (r["ms"] * 1e-3)
     # dominant fused call and its algorithmic bytes per launch
     if r["ms_bwd"] >= r["ms_fwd"]:
@@ -708,14 +788,17 @@ def main():
         cb, _, parity = cpu_baseline(args, gpu_out=r["sample_out"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": scaling,
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "layout": LAYOUT_NOTE[args.layout],
                    "instances_per_gpu": lay.count, "band_entries_per_gpu": r["entries"],
                    "rows_per_gpu": int(sum(lay.ns)), "k": lay.k, "seg_len": args.seg_len or ("library default: 384" if args.layout == "panels" else "library default: 2048"), "warmup_rows": args.warm or (f"{args.warm_per_l} l + {args.warm_base}" if args.warm_per_l else "library default"),
                    "chains": r["plan"].chains, "warp_tasks": r["plan"].tasks, "graph": True,
                    "l2": "inputs (~%.1f GB) exceed L2; no flush" % (r["h2d"] / 1e9),
-                   "parallelism": f"instances sharded per GPU (weak), dp{world}", "segment_fixups": r["fixups"]},
+                   "parallelism": (f"one batch of {args.count} instances split by shard.partition (strong), "
+                                   f"dp{world}" if scaling == "strong" else
+                                   f"a batch of {args.count} instances per GPU (weak), dp{world}"),
+                   "segment_fixups": r["fixups"]},
         "e2e": {"value": entries_all / (r["ms_e2e"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"], "ms_per_step": r["ms_e2e"]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],

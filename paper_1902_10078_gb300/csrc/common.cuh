@@ -123,6 +123,8 @@ struct bnd_plan {
     int32_t *group_first;      // panel plans: groups (ngroups + 1 entries)
     int32_t ngroups;
     int32_t has_generic;       // some instance runs the generic (any-bandwidth) path
+    int32_t wide_cta;          // the block kernels serve the generic class (its windows fit)
+    int32_t wide_segmented;    // some generic-class instance is cut into segments
     // tasks are grouped by bandwidth class: class 0 = generic (l = 0 or l > kRegMaxL),
     // class c = bandwidth c; class c owns tasks [class_task0[c], class_task0[c+1])
     int32_t class_task0[bnd::kRegMaxL + 2];

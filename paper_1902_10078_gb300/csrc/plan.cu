@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sweep_cta.cuh"
 
 using namespace bnd;
 
@@ -28,6 +29,10 @@ constexpr int64_t kDefaultSegLenPanels = 384;
 // time of a sweep is that of one chain, segment plus warm-up rows.
 constexpr int64_t kTargetChains = 16384;
 constexpr int64_t kMinSegLen = 32;
+// Wide bands (one thread block per segment): the time of a sweep is that of
+// its longest segment, so the wide instances are cut into about one segment
+// per SM of a GB300 (152) in all, each at least one warm-up long.
+constexpr int64_t kWideTargetSegs = 152;
 
 // Default warm-up of a speculative segment start.  The cold-started state
 // forgets its start at a rate per block of l rows, so the warm-up grows with
@@ -125,6 +130,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     const size_t esz = dtype == BND_F32 ? 4 : 8;
     p->warm = 0;                                      // 0: per-bandwidth default
     p->seg_len = 0;
+    const int64_t user_seg_len = tuning ? tuning->seg_len : 0;
     if (tuning) {
         if (tuning->seg_len != 0) p->seg_len = tuning->seg_len;
         if (tuning->warmup > 0) p->warm = tuning->warmup;
@@ -169,6 +175,17 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
             p->seg_len = std::max<int64_t>(kMinSegLen, (lane_rows / kTargetChains + 3) / 4 * 4);
     }
 
+    // wide-band instances (l = 0 or above the register-window limit) run on the block kernels
+    // when the widest one's windows fit; those with l > 0 are then segmented too
+    int32_t max_wide_l = -1;
+    int64_t wide_rows = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (inst[i].l >= 1 && inst[i].l <= kRegMaxL) continue;
+        max_wide_l = std::max(max_wide_l, inst[i].l);
+        if (inst[i].l > 0) wide_rows += inst[i].n;
+    }
+    p->wide_cta = max_wide_l >= 0 && (dtype == BND_F32 ? cta_fits<float>(max_wide_l) : cta_fits<double>(max_wide_l));
+
     std::vector<InstDev> idev((size_t)count);
     int64_t nsegs = 0;
     int32_t max_l = 0;
@@ -189,7 +206,15 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         int64_t seg_len = p->seg_len;
         if (seg_len > 0 && p->seg_by_warm) seg_len = std::max<int64_t>(64, seg_len * D.warm / 128);
         int64_t nseg = 1, len = I.n;
-        if (panels) {
+        if (!reg) {
+            if (p->wide_cta && I.l > 0 && p->seg_len > 0) {
+                const int64_t wl = user_seg_len > 0 ? user_seg_len
+                                                    : std::max<int64_t>(D.warm, (wide_rows + kWideTargetSegs - 1) /
+                                                                                    kWideTargetSegs);
+                segmentation(I.n, wl, D.warm, true, &nseg, &len);
+            }
+            if (!panels && (I.band % tw || I.ld % tw || (k > 0 && (I.rhs % tw || I.ldr % tw)))) p->staged_ok = 0;
+        } else if (panels) {
             // one segment length for the whole group, set by its longest member
             const int32_t g = group_of[(size_t)i], g0 = groups[(size_t)g], g1 = groups[(size_t)g + 1];
             int64_t gn = 0;
@@ -214,6 +239,13 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->band_pool_elems = band_extent;
     p->rhs_pool_elems = rhs_extent;
     p->snap_words = snap_words_for(std::min(max_l, kRegMaxL), std::max(k, kMaxK));
+    for (int32_t i = 0; i < count; ++i) {
+        const InstDev &D = idev[(size_t)i];
+        if (D.nseg > 1 && !(D.l >= 1 && D.l <= kRegMaxL)) {
+            p->wide_segmented = 1;
+            p->snap_words = std::max<int64_t>(p->snap_words, cta_state_words(D.l));
+        }
+    }
 
     struct TaskTmp { std::vector<Chain> c; int32_t l; int32_t cls; double cost; Task geo; };
     auto class_of = [](int l) { return (l >= 1 && l <= kRegMaxL) ? l : 0; };

@@ -24,6 +24,13 @@
 // Per row: three block barriers (load / finish the row's scalars / window
 // update).  The O(l^2) work of a row (rank-1 window update, or a matrix-vector
 // product with a window and a rank-1 update) is spread over the block.
+//
+// Segments.  A long instance is cut into segments run by separate blocks; a
+// segment other than the first in sweep order starts `warm` rows early from a
+// zero state (cold start) and saves the state it reached at its first output
+// row, and every segment saves its state after its last row.  A verify pass
+// then compares each boundary and reruns from the exact state the segments
+// whose start was not close enough (cta_states_close).
 #pragma once
 
 #include "sweep_impl.cuh"
@@ -42,9 +49,18 @@ __host__ __device__ inline int64_t cta_smem_elems(int l) {
     const int64_t lw = l + 1;
     return lw * lw + 2 * (int64_t)kCtaMaxK * lw + 6 * lw + 2 * kCtaWarps + 4 * kCtaMaxK + 8;
 }
-// The block sweeps serve bandwidth l in dtype T when its windows fit.
+// The block sweeps serve bandwidth l in dtype T when its windows fit (1 KB is
+// left for the verify kernel's static shared memory).
 template <typename T>
-__host__ __device__ inline bool cta_fits(int l) { return sizeof(T) * (size_t)cta_smem_elems(l) <= kCtaSmemLimit; }
+__host__ __device__ inline bool cta_fits(int l) {
+    return sizeof(T) * (size_t)cta_smem_elems(l) <= kCtaSmemLimit - 1024;
+}
+// Words of a block sweep's state snapshot: the band window and the RHS ring,
+// rotated so that the slot of the current column comes first.
+__host__ __device__ inline int64_t cta_state_words(int l) {
+    const int64_t lw = l + 1;
+    return lw * lw + (int64_t)kCtaMaxK * lw;
+}
 
 template <typename T>
 __device__ __forceinline__ T cta_block_sum(T v, T *red) {
@@ -93,11 +109,114 @@ struct FoldIter {
 
 __device__ __forceinline__ int wrap_slot(int s, int lw) { return s >= lw ? s - lw : (s < 0 ? s + lw : s); }
 
+// Save (or load) the state of a block sweep whose current column has slot sj:
+// word x < (l+1)^2 is entry f of the window column rel slots after sj
+// (x = rel (l+1) + f), then RHS ring row r, rel slots after sj.  Whole block.
+template <typename T>
+__device__ void cta_state_io(T *W, T *U, int l, int sj, T *snap, bool save) {
+    const int lw = l + 1, nw = lw * lw;
+    __syncthreads();
+    for (int x = threadIdx.x; x < nw + kCtaMaxK * lw; x += kCtaThreads) {
+        T *live;
+        if (x < nw) {
+            const int rel = x / lw, f = x - rel * lw;
+            live = W + wrap_slot(sj + rel, lw) * lw + f;
+        } else {
+            const int y = x - nw, r = y / lw, rel = y - r * lw;
+            live = U + r * lw + wrap_slot(sj + rel, lw);
+        }
+        if (save) snap[x] = *live;
+        else *live = snap[x];
+    }
+    __syncthreads();
+}
+
+// Acceptance of a speculative segment start.  Once a cold start has forgotten
+// its zero state mathematically, the two runs differ only by rounding, but
+// above l of about 50 they never become equal bit for bit: a one-ulp
+// difference in one window entry reaches l others through the row's O(l^2)
+// update, and enough of those survive rounding to keep the difference alive
+// for good, at about one ulp of the state's largest entry -- the rounding
+// noise either run carries anyway.  (At l <= 32 the difference dies out within
+// a few blocks of l rows, as it does for the register-window sweeps, which
+// compare bit for bit.)  So a boundary passes when the two snapshots agree
+// word for word within StateTol times the largest magnitude of their part of
+// the state (the band window as a whole; each RHS row on its own); a start
+// that has not converged is off by orders of magnitude more.  Bitwise-equal
+// words always agree (NaN included); any other NaN fails.
+template <typename T> struct StateTol;
+template <> struct StateTol<float> { static constexpr float value = 1.52587890625e-05f; };        // 2^-16
+template <> struct StateTol<double> { static constexpr double value = 5.684341886080802e-14; };   // 2^-44
+
+template <typename T>
+__device__ __forceinline__ void state_word_cmp(T a, T b, T &dmax, T &amax, bool &bad) {
+    const bool same = sizeof(T) == 4 ? __float_as_uint((float)a) == __float_as_uint((float)b)
+                                     : __double_as_longlong((double)a) == __double_as_longlong((double)b);
+    if (same) {
+        if (a == a) amax = fmax(amax, fabs(a));
+        return;
+    }
+    const T d = fabs(a - b);
+    if (!(d == d)) bad = true;
+    else dmax = fmax(dmax, d);
+    amax = fmax(amax, fmax(fabs(a), fabs(b)));
+}
+
+// Whole block: true when snapshots x and y (cta_state_io layout, bandwidth l)
+// are close in the sense above.
+template <typename T>
+__device__ bool cta_states_close(const T *x, const T *y, int l) {
+    __shared__ T buf[2 * kCtaWarps];
+    const int lw = l + 1, nw = lw * lw;
+    const int tid = threadIdx.x, warp = tid / kWarp, lane = tid % kWarp;
+    const T tol = StateTol<T>::value;
+    bool ok = true;
+    T dm = T(0), am = T(0);
+    bool bad = false;
+    for (int w = tid; w < nw; w += kCtaThreads) state_word_cmp(x[w], y[w], dm, am, bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+    }
+    if (lane == 0) { buf[warp] = dm; buf[kCtaWarps + warp] = am; }
+    for (int r = warp; r < kCtaMaxK; r += kCtaWarps) {       // RHS row r: warp r
+        T rd = T(0), ra = T(0);
+        bool rb = false;
+        for (int i = lane; i < lw; i += kWarp) state_word_cmp(x[nw + r * lw + i], y[nw + r * lw + i], rd, ra, rb);
+        rb = __any_sync(0xffffffffu, rb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rd = fmax(rd, __shfl_xor_sync(0xffffffffu, rd, o));
+            ra = fmax(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+        }
+        if (rb || !(rd <= tol * ra)) ok = false;
+    }
+    if (bad) ok = false;
+    __syncthreads();
+    T wd = T(0), wa = T(0);
+    for (int w = 0; w < kCtaWarps; ++w) {
+        wd = fmax(wd, buf[w]);
+        wa = fmax(wa, buf[kCtaWarps + w]);
+    }
+    if (!(wd <= tol * wa)) ok = false;
+    return __syncthreads_and(ok) != 0;        // its barrier also keeps buf until every thread has read it
+}
+
+// First row of a block sweep over chain c (forward: the rows run upward from
+// it; backward: downward): a cold start of a segment that is not the first in
+// sweep order begins `warm` rows outside the segment.
+__device__ __forceinline__ int64_t cta_first_row(const ChainCtx &c, bool fwd, int mode) {
+    if (fwd) return (mode == RUN_COLD && !c.first) ? imax64(c.a - c.warm, 0) : c.a;
+    return (mode == RUN_COLD && !c.last) ? imin64(c.b - 1 + c.warm, c.n - 1) : c.b - 1;
+}
+
 // ===========================================================================
 // Forward: CHOL [+ SOLVE], SOLVE, ALG4 [+ SOLVE]; one block per chain.
 // ===========================================================================
 template <typename T, int FL>
-__device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, T *sm) {
+__device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, T *sm, int mode,
+                            const T *exact) {
     constexpr bool CHOL = (FL & F_CHOL) != 0, ALG4 = (FL & F_ALG4) != 0;
     const bool SOLVE = (FL & F_SOLVE) != 0 && P.k > 0;
     const int kk = SOLVE ? A.kk : 0;
@@ -123,10 +242,13 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
     T *Lbo = ALG4 ? A.Lbar + c.band : nullptr;
     const T *Bi = SOLVE ? A.Bin + c.rhs : nullptr;
     T *Xo = SOLVE ? A.Xout + c.rhs : nullptr;
-    double ldacc = 0.0;
     int32_t info = 0;
-    int sj = 0;                                  // slot of column j: j mod (l + 1)
-    for (int64_t j = 0; j < n; ++j, sj = wrap_slot(sj + 1, lw)) {
+    const int64_t j0 = cta_first_row(c, true, mode);
+    int sj = (int)(j0 % lw);                     // slot of column j: j mod (l + 1)
+    if (mode == RUN_EXACT && exact) cta_state_io(W, U, l, sj, const_cast<T *>(exact), false);
+    for (int64_t j = j0; j < c.b; ++j, sj = wrap_slot(sj + 1, lw)) {
+        const bool out = j >= c.a;                // warm-up rows only carry the state
+        if (j == c.a && !c.first) cta_state_io(W, U, l, sj, snap_ptr<T>(P, c.gseg, 0), true);
         const int dmax = (int)imin64(l, n - 1 - j);
         // ---- phase A: the row's inputs, the retired window column
         for (int d = tid; d <= l; d += kCtaThreads) {
@@ -154,14 +276,11 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         if (CHOL) {
             const T piv = av[0];
             rinv = Num<T>::rsq(piv);
-            if (tid == 0) {
-                if (!(piv > T(0)) && info == 0) info = (int32_t)(j + 1);
-                ldacc += log((double)piv);
-            }
+            if (out && tid == 0 && !(piv > T(0)) && info == 0) info = (int32_t)(j + 1);
             for (int d = tid; d <= l; d += kCtaThreads) {
                 const T v = (d == 0) ? piv * rinv : av[d] * rinv;
                 lc[d] = d <= dmax ? v : T(0);
-                Lo[(int64_t)d * ld + j * cs] = d <= dmax ? v : T(0);
+                if (out) Lo[(int64_t)d * ld + j * cs] = d <= dmax ? v : T(0);
             }
         } else {
             rinv = Num<T>::rcp(lc[0]);
@@ -171,7 +290,7 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
             if (tid < kk) {
                 const T y = yv[tid] * rinv;
                 yv[tid] = y;
-                Xo[(int64_t)(A.rhs0 + tid) * c.ldr + j * cs] = y;
+                if (out) Xo[(int64_t)(A.rhs0 + tid) * c.ldr + j * cs] = y;
             }
         }
         if (ALG4) {
@@ -216,7 +335,7 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 const T v = bu[t] - acc;
                 if (lane == 0) {
-                    if (t <= dmax) {
+                    if (out && t <= dmax) {
                         T *p = &Lbo[(int64_t)t * ld + i * cs];
                         const T o = v * rinv;
                         *p = A.acc ? (*p + o) : o;
@@ -236,7 +355,7 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
             }
             // diagonal of L-bar: -2 b0 / L_ii^3 - (sum_t bU[t] L[i+t, i]) / L_ii^2
             const T s = cta_block_sum(part, red);
-            if (tid == 0) {
+            if (out && tid == 0) {
                 const T r2 = rinv * rinv;
                 const T o = T(-2) * av[0] * r2 * rinv - s * r2;
                 T *p = &Lbo[i * cs];
@@ -246,9 +365,32 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         }
         __syncthreads();
     }
-    if (CHOL && tid == 0) {
-        if (A.logdet) A.logdet[c.inst] = info ? (double)NAN : ldacc;
-        A.info[c.inst] = info;
+    if (!c.last) cta_state_io(W, U, l, sj, snap_ptr<T>(P, c.gseg, 1), true);
+    if (CHOL) {
+        // log det Q = 2 sum_j log L_jj over the segment's rows, summed by the whole block from
+        // the diagonal it wrote (a logarithm per row on one thread would sit on every row's
+        // critical path: FP64 is slow on this part)
+        double part = 0.0;
+        for (int64_t j = c.a + tid; j < c.b; j += kCtaThreads) part += log((double)Lo[j * cs]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        double *dred = reinterpret_cast<double *>(sm);
+        __syncthreads();
+        if (lane == 0) dred[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            double ldacc = 0.0;
+            for (int w = 0; w < kCtaWarps; ++w) ldacc += dred[w];
+            ldacc *= 2.0;
+            if (c.first && c.last) {
+                if (A.logdet) A.logdet[c.inst] = info ? (double)NAN : ldacc;
+                A.info[c.inst] = info;
+            } else {
+                P.seg_logdet[c.gseg] = ldacc;
+                P.seg_info[c.gseg] = info;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -256,7 +398,8 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
 // Backward: TAKA [+ SOLVE], SOLVE, ALG2 [+ SOLVE + OUTER]; one block per chain.
 // ===========================================================================
 template <typename T, int FL>
-__device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, T *sm) {
+__device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const ChainCtx &c, T *sm, int mode,
+                            const T *exact) {
     constexpr bool TAKA = (FL & B_TAKA) != 0, ALG2 = (FL & B_ALG2) != 0;
     const bool SOLVE = (FL & B_SOLVE) != 0 && P.k > 0;
     const bool OUTER = (FL & B_OUTER) != 0 && SOLVE && ALG2;
@@ -282,8 +425,12 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
     const T *Xi = OUTER ? A.Xin + c.rhs : nullptr;
     const T two_ldbar = (ALG2 && A.ldbar) ? T(2.0 * A.ldbar[c.inst]) : T(0);
 #define LIN(r_, m_) Li[(int64_t)((r_) - (m_)) * ld + (m_) * cs]
-    int sj = (int)((n - 1) % lw);                // slot of column j: j mod (l + 1)
-    for (int64_t j = n - 1; j >= 0; --j, sj = wrap_slot(sj - 1, lw)) {
+    const int64_t j0 = cta_first_row(c, false, mode);
+    int sj = (int)(j0 % lw);                     // slot of column j: j mod (l + 1)
+    if (mode == RUN_EXACT && exact) cta_state_io(W, U, l, sj, const_cast<T *>(exact), false);
+    for (int64_t j = j0; j >= c.a; --j, sj = wrap_slot(sj - 1, lw)) {
+        const bool out = j < c.b;                 // warm-up rows only carry the state
+        if (j == c.b - 1 && !c.last) cta_state_io(W, U, l, sj, snap_ptr<T>(P, c.gseg, 0), true);
         const int dmax = (int)imin64(l, n - 1 - j);
         // ---- phase A: column j of L; SOLVE reductions x_j = (b_j - sum_d L[j+d,j] x_{j+d}) / L_jj
         for (int d = tid; d <= l; d += kCtaThreads) lc[d] = d <= dmax ? Li[(int64_t)d * ld + j * cs] : T(0);
@@ -315,7 +462,7 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
                 const T xj = (bj - acc) * rinv;
                 sc[r] = xj;
                 sc[2 * kCtaMaxK + r] = bj;              // ybar of the OUTER term (Bin = Ybar)
-                Xo[co + j * cs] = xj;
+                if (out) Xo[co + j * cs] = xj;
             }
             if (OUTER) {
                 T y = T(0);
@@ -349,7 +496,7 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
             // outputs, then the new window column i: Sigma(i+q, i) for q = 0..l-1
             for (int q = tid; q <= l; q += kCtaThreads) {
                 const T v = q == 0 ? diag : rw[q];
-                So[(int64_t)q * ld + i * cs] = q <= dmax ? v : T(0);
+                if (out) So[(int64_t)q * ld + i * cs] = q <= dmax ? v : T(0);
                 if (q < l) W[sj * lw + q] = q <= dmax ? v : T(0);
             }
         }
@@ -378,7 +525,7 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
             }
             const T s = cta_block_sum(part, red);        // (its barrier also publishes rw)
             const T qb0 = T(0.5) * (rw[0] + s) * rinv;
-            for (int d = tid; d <= l; d += kCtaThreads) {
+            for (int d = tid; out && d <= l; d += kCtaThreads) {
                 const T v = d == 0 ? qb0 : rw[d];
                 T *p = &Qo[(int64_t)d * ld + j * cs];
                 *p = d <= dmax ? (A.acc ? (*p + v) : v) : T(0);
@@ -404,7 +551,15 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
             }
         }
         __syncthreads();
+        // column j + l leaves the TAKA window and the x ring (row j - 1 reads columns j ..
+        // j + l - 1) and its slot is the next row's: cleared, so that a saved state holds
+        // live columns only
+        const int sx = wrap_slot(sj + l, lw);
+        for (int r = tid; SOLVE && r < kk; r += kCtaThreads) U[r * lw + sx] = T(0);
+        if (TAKA)
+            for (int f = tid; f < lw; f += kCtaThreads) W[sx * lw + f] = T(0);
     }
+    if (!c.first) cta_state_io(W, U, l, sj, snap_ptr<T>(P, c.gseg, 1), true);
 #undef LIN
 }
 

@@ -161,8 +161,79 @@ __global__ void __launch_bounds__(kCtaThreads) cta_kernel(PlanDev P, SweepArgs<T
     if (ch.inst < 0) return;
     const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
     T *sm = reinterpret_cast<T *>(smem_raw);
-    if constexpr (FWD) run_fwd_cta<T, FL>(P, A, c, sm);
-    else run_bwd_cta<T, FL>(P, A, c, sm);
+    if constexpr (FWD) run_fwd_cta<T, FL>(P, A, c, sm, RUN_COLD, nullptr);
+    else run_bwd_cta<T, FL>(P, A, c, sm, RUN_COLD, nullptr);
+}
+
+// Segment boundaries of the block sweeps, compared in parallel: block w takes
+// chain chain0 + w (instance i, segment b >= 1) and flags boundary b of i
+// (between segments b-1 and b) in chain_flag when the state the later segment
+// in sweep order started from speculatively is not close to the end state
+// its neighbour left.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kCtaThreads) cta_compare_kernel(PlanDev P, int64_t chain0, int64_t nchains) {
+    const int64_t w = blockIdx.x;
+    if (w >= nchains) return;
+    const Chain ch = P.chains[chain0 + w];
+    if (ch.inst < 0 || ch.seg == 0) return;
+    const InstDev I = P.inst[ch.inst];
+    const int64_t g = I.seg0 + ch.seg;
+    const T *x = FWD ? snap_ptr<T>(P, g - 1, 1) : snap_ptr<T>(P, g, 1);
+    const T *y = FWD ? snap_ptr<T>(P, g, 0) : snap_ptr<T>(P, g - 1, 0);
+    const bool ok = cta_states_close(x, y, I.l);
+    if (threadIdx.x == 0) P.chain_flag[chain0 + w] = ok ? 0 : 1;
+}
+
+// Fixup of the segmented block-sweep instances: one block per instance.  From
+// the first flagged boundary in sweep order the block reruns, one after the
+// other, every segment whose start state is still not close to the end state
+// its (possibly rerun) neighbour left, from that exact state; the flags are
+// cleared for the next launch.  The segments' log-det / info are reduced by
+// verify_kernel after.
+template <typename T, int K, int FL, bool FWD>
+__global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, SweepArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const InstDev I = P.inst[blockIdx.x];
+    if ((I.l >= 1 && I.l <= kRegMaxL) || I.nseg <= 1) return;
+    __shared__ int first_s;
+    auto boundary_ok = [&](int b) {           // whole block; b joins segments b-1 and b
+        const int64_t g = I.seg0 + b;
+        const T *x = FWD ? snap_ptr<T>(P, g - 1, 1) : snap_ptr<T>(P, g, 1);
+        const T *y = FWD ? snap_ptr<T>(P, g, 0) : snap_ptr<T>(P, g - 1, 0);
+        return cta_states_close(x, y, I.l);
+    };
+    if (threadIdx.x == 0) first_s = FWD ? I.nseg : 0;
+    __syncthreads();
+    for (int b = 1 + (int)threadIdx.x; b < I.nseg; b += kCtaThreads) {
+        uint8_t *f = P.chain_flag + P.seg_chain[I.seg0 + b];
+        if (*f) {
+            if (FWD) atomicMin(&first_s, b);
+            else atomicMax(&first_s, b);
+            *f = 0;
+        }
+    }
+    __syncthreads();
+    const int first = first_s;
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    unsigned int fixes = 0;
+    if (FWD) {
+        for (int b = first; b < I.nseg; ++b) {
+            if (b > first && boundary_ok(b)) continue;
+            __syncthreads();
+            run_fwd_cta<T, FL>(P, A, make_ctx(P, blockIdx.x, b), sm, RUN_EXACT, snap_ptr<T>(P, I.seg0 + b - 1, 1));
+            __syncthreads();
+            ++fixes;
+        }
+    } else {
+        for (int b = first; b >= 1; --b) {
+            if (b < first && boundary_ok(b)) continue;
+            __syncthreads();
+            run_bwd_cta<T, FL>(P, A, make_ctx(P, blockIdx.x, b - 1), sm, RUN_EXACT, snap_ptr<T>(P, I.seg0 + b, 1));
+            __syncthreads();
+            ++fixes;
+        }
+    }
+    if (threadIdx.x == 0 && fixes) atomicAdd(P.counters + kNumSweepKinds + A.kind, fixes);
 }
 
 template <typename T, int K, int FL, bool FWD>
@@ -178,6 +249,19 @@ static cudaError_t launch_wide(const bnd_plan *p, const SweepArgs<T> &A, int32_t
         if (ok <= 0) return cudaErrorInvalidValue;
         const int64_t nch = (int64_t)nt * kWarp;
         cta_kernel<T, K, FL, FWD><<<(unsigned)nch, kCtaThreads, cta_bytes, s>>>(p->dev, A, (int64_t)t0 * kWarp, nch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || !p->wide_segmented) return e;
+        static PerDeviceSlots vattr;
+        const int vok = per_device(vattr, [] {
+            // the verify kernel has a few hundred bytes of static shared memory besides the window
+            return cudaFuncSetAttribute(cta_verify_kernel<T, K, FL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kCtaSmemLimit - 1024) == cudaSuccess ? 1 : -1;
+        });
+        if (vok <= 0) return cudaErrorInvalidValue;
+        cta_compare_kernel<T, FWD><<<(unsigned)nch, kCtaThreads, 0, s>>>(p->dev, (int64_t)t0 * kWarp, nch);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        cta_verify_kernel<T, K, FL, FWD><<<(unsigned)p->count, kCtaThreads, cta_bytes, s>>>(p->dev, A);
         return cudaGetLastError();
     }
     // windows too large for shared memory: one warp per chain, windows in global memory
@@ -329,7 +413,15 @@ static cudaError_t launch_sweep_t(const bnd_plan *p, const SweepArgs<T> &A, cuda
     cudaError_t e = cudaSuccess;
     const bool staged = p->layout != kLayoutStrided && p->staged_ok && args_aligned16(A) && !p->force_direct;
     if (!staged) {
-        e = launch_direct<T, K, FL, FWD>(p, A, 0, p->ntasks, s);
+        // the block kernels need no alignment beyond the element size: they keep the generic
+        // class (segmented or not) whenever their windows fit
+        const int32_t nwide = p->class_task0[1] - p->class_task0[0];
+        if (p->wide_cta && nwide > 0) {
+            e = launch_wide<T, K, FL, FWD>(p, A, p->class_task0[0], nwide, s);
+            if (e == cudaSuccess) e = launch_direct<T, K, FL, FWD>(p, A, p->class_task0[1], p->ntasks - p->class_task0[1], s);
+        } else {
+            e = launch_direct<T, K, FL, FWD>(p, A, 0, p->ntasks, s);
+        }
     } else {
         // fork: one side stream per bandwidth class, each waiting on the main stream
         e = cudaEventRecord(p->ev_fork, s);

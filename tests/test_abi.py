@@ -82,11 +82,29 @@ def test_plan_never_splits_when_asked(lib):
         B.bnd_plan_destroy(p)
 
 
-def test_plan_keeps_wide_bands_whole(lib):
-    # bandwidths above the register-window limit run one chain per instance
+def test_plan_segments_wide_bands_on_the_block_kernels(lib):
+    # bandwidths above the register-window limit run on the block kernels, which take
+    # segments too (here the asked 1024 rows); without a length, about one segment per
+    # SM (152) over all wide instances, each at least one warm-up long (16 l + 32 rows in
+    # FP32, 48 l + 64 in FP64); seg_len = -1 keeps them whole
     p = B.bnd_plan_create(B.BND_F64, _insts([50000, 50000], [12, 3]), 1, dict(seg_len=1024))
     try:
-        assert B.bnd_plan_chains(p) == 1 + 49
+        assert B.bnd_plan_chains(p) == 49 + 49
+    finally:
+        B.bnd_plan_destroy(p)
+    p = B.bnd_plan_create(B.BND_F64, _insts([200000], [64]), 1)
+    try:
+        assert B.bnd_plan_chains(p) == round(200000 / (48 * 64 + 64))
+    finally:
+        B.bnd_plan_destroy(p)
+    p = B.bnd_plan_create(B.BND_F32, _insts([200000], [64]), 1)
+    try:
+        assert B.bnd_plan_chains(p) == 152
+    finally:
+        B.bnd_plan_destroy(p)
+    p = B.bnd_plan_create(B.BND_F64, _insts([50000], [12]), 1, dict(seg_len=-1))
+    try:
+        assert B.bnd_plan_chains(p) == 1
     finally:
         B.bnd_plan_destroy(p)
 
