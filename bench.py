@@ -604,7 +604,7 @@ def run_config(args):
         for l in args.wide_ls:
             for name in args.wide_dtypes:
                 dt = dts[name]
-                n, k = 200_000, 16
+                n, k = args.wide_n, 16
                 tuning = {key: v for key, v in (("seg_len", args.seg_len), ("warm_per_l", args.warm_per_l),
                                                  ("warm_base", args.warm_base)) if v}
                 lay, plan, step, info = gmm_setup([(n, l)], k, dt, tuning or None)
@@ -662,10 +662,11 @@ def run_config(args):
         n = Qg.shape[1]
         ins = W.make_instance(n, l, 1, W.BASE_SEED)
         ins.Q = Qg
-        for name in args.wide_dtypes:
+        variants = [(name, None) for name in args.wide_dtypes] + [(name, -1) for name in args.wide_dtypes]
+        for name, seg in variants:
             dt = dts[name]
-            tuning = {key: v for key, v in (("seg_len", args.seg_len), ("warm_per_l", args.warm_per_l),
-                                             ("warm_base", args.warm_base)) if v}
+            tuning = {key: v for key, v in (("seg_len", args.seg_len if seg is None else seg),
+                                             ("warm_per_l", args.warm_per_l), ("warm_base", args.warm_base)) if v}
             lay = BT.Layout([n], [l], 1, dt)
             plan = BT.Plan(lay, tuning or None)
             dev = {key: torch.from_numpy(pool).cuda() for key, pool in (
@@ -727,6 +728,7 @@ def main():
                     help="time another workload configuration instead of the uneven batch")
     ap.add_argument("--wide-ls", type=int, nargs="+", default=[64, 128], help="bandwidths of --config 3")
     ap.add_argument("--wide-dtypes", nargs="+", default=["f32", "f64"], help="dtypes of --config 3")
+    ap.add_argument("--wide-n", type=int, default=200_000, help="rows of --config 3 (smaller: profiling cases)")
     ap.add_argument("--profile-once", action="store_true",
                     help="run one forward and one backward call in NVTX ranges (for ncu) and exit")
     ap.add_argument("--summarize-ncu", default=None, help="ncu --csv file of one backward call -> profiles/")

@@ -216,10 +216,12 @@ def _cuda_timer(fn, reps, warmup):
 
 
 # Default candidates: segment length x warm-up slope (rows per unit of bandwidth,
-# plus 32), and the direct kernels at the library defaults.
+# plus 32), the direct kernels at the library defaults, and no segmentation at
+# all (for inputs whose cold starts converge too slowly: every segment would be
+# rerun after the parallel pass).
 DEFAULT_CANDIDATES = tuple(
     [dict(seg_len=s, warm_per_l=w, warm_base=32) for s in (256, 384, 512, 768) for w in (12, 16, 24)]
-    + [dict(flags=1)])
+    + [dict(flags=1), dict(seg_len=-1)])
 
 
 def _candidate_key(c):

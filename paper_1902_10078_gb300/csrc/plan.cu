@@ -45,6 +45,17 @@ int64_t default_warm(bnd_dtype dt, int l) {
     const int64_t w = dt == BND_F32 ? 16 * (int64_t)l + 32 : 48 * (int64_t)l + 64;
     return (w + 3) / 4 * 4;
 }
+// Wide bands accept a segment start within the rounding noise of the state
+// (not bit for bit), which a cold start reaches in fewer rows.  Measured on the
+// wide-band workload (n = 2e5, l = 64 and 128, 16 right-hand sides): no rerun
+// from 8 l + 32 rows (FP32) and 16 l + 64 (FP64) on, and every shorter
+// warm-up of the sweep ran faster (FP32 l = 64: 31.4 ms per fused step at
+// 8 l + 32 vs 39.7 at 16 l + 32; FP64 l = 128: 332 ms at 16 l + 64 vs 977 at
+// 48 l + 64).
+int64_t default_warm_wide(bnd_dtype dt, int l) {
+    const int64_t w = dt == BND_F32 ? 8 * (int64_t)l + 32 : 16 * (int64_t)l + 64;
+    return (w + 3) / 4 * 4;
+}
 constexpr int32_t kMaxBand = 1024;
 constexpr int32_t kMaxRhs = 64;
 
@@ -184,7 +195,8 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         max_wide_l = std::max(max_wide_l, inst[i].l);
         if (inst[i].l > 0) wide_rows += inst[i].n;
     }
-    p->wide_cta = max_wide_l >= 0 && (dtype == BND_F32 ? cta_fits<float>(max_wide_l) : cta_fits<double>(max_wide_l));
+    p->wide_cta = max_wide_l >= 0 && (dtype == BND_F32 ? cta_serves<float>(max_wide_l, cta_rhs(k))
+                                                       : cta_serves<double>(max_wide_l, cta_rhs(k)));
 
     std::vector<InstDev> idev((size_t)count);
     int64_t nsegs = 0;
@@ -200,7 +212,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         if (!reg) has_generic = true;
         if (p->warm > 0) D.warm = ((int64_t)p->warm + 3) / 4 * 4;
         else if (p->warm_per_l > 0) D.warm = ((int64_t)p->warm_per_l * I.l + p->warm_base + 3) / 4 * 4;
-        else D.warm = default_warm(dtype, I.l);
+        else D.warm = (!reg && p->wide_cta) ? default_warm_wide(dtype, I.l) : default_warm(dtype, I.l);
         // segment length: the same for every bandwidth, or (flag) scaled with the warm-up so
         // that every bandwidth pays the same fraction of extra rows (seg_len at 128 warm-up rows)
         int64_t seg_len = p->seg_len;
@@ -243,7 +255,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
         const InstDev &D = idev[(size_t)i];
         if (D.nseg > 1 && !(D.l >= 1 && D.l <= kRegMaxL)) {
             p->wide_segmented = 1;
-            p->snap_words = std::max<int64_t>(p->snap_words, cta_state_words(D.l));
+            p->snap_words = std::max<int64_t>(p->snap_words, cta_state_words(D.l, cta_rhs(k)));
         }
     }
 

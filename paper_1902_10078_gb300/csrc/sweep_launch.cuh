@@ -153,7 +153,8 @@ wide_kernel(PlanDev P, SweepArgs<T> A, int64_t chain0, int64_t nchains) {
 // instance fits the per-block shared memory.
 
 template <typename T, int K, int FL, bool FWD>
-__global__ void __launch_bounds__(kCtaThreads) cta_kernel(PlanDev P, SweepArgs<T> A, int64_t chain0, int64_t nchains) {
+__global__ void __launch_bounds__(kCtaThreads) cta_kernel(PlanDev P, SweepArgs<T> A, int64_t chain0, int64_t nchains,
+                                                          int tier) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t w = blockIdx.x;
     if (w >= nchains) return;
@@ -161,8 +162,8 @@ __global__ void __launch_bounds__(kCtaThreads) cta_kernel(PlanDev P, SweepArgs<T
     if (ch.inst < 0) return;
     const ChainCtx c = make_ctx(P, ch.inst, ch.seg);
     T *sm = reinterpret_cast<T *>(smem_raw);
-    if constexpr (FWD) run_fwd_cta<T, FL>(P, A, c, sm, RUN_COLD, nullptr);
-    else run_bwd_cta<T, FL>(P, A, c, sm, RUN_COLD, nullptr);
+    if constexpr (FWD) run_fwd_cta<T, FL>(P, A, c, sm, RUN_COLD, nullptr, tier);
+    else run_bwd_cta<T, FL>(P, A, c, sm, RUN_COLD, nullptr, tier);
 }
 
 // Segment boundaries of the block sweeps, compared in parallel: block w takes
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kCtaThreads) cta_compare_kernel(PlanDev P, int
     const int64_t g = I.seg0 + ch.seg;
     const T *x = FWD ? snap_ptr<T>(P, g - 1, 1) : snap_ptr<T>(P, g, 1);
     const T *y = FWD ? snap_ptr<T>(P, g, 0) : snap_ptr<T>(P, g - 1, 0);
-    const bool ok = cta_states_close(x, y, I.l);
+    const bool ok = cta_states_close(x, y, I.l, cta_rhs(P.k));
     if (threadIdx.x == 0) P.chain_flag[chain0 + w] = ok ? 0 : 1;
 }
 
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kCtaThreads) cta_compare_kernel(PlanDev P, int
 // cleared for the next launch.  The segments' log-det / info are reduced by
 // verify_kernel after.
 template <typename T, int K, int FL, bool FWD>
-__global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, SweepArgs<T> A) {
+__global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, SweepArgs<T> A, int tier) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const InstDev I = P.inst[blockIdx.x];
     if ((I.l >= 1 && I.l <= kRegMaxL) || I.nseg <= 1) return;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, Swee
         const int64_t g = I.seg0 + b;
         const T *x = FWD ? snap_ptr<T>(P, g - 1, 1) : snap_ptr<T>(P, g, 1);
         const T *y = FWD ? snap_ptr<T>(P, g, 0) : snap_ptr<T>(P, g - 1, 0);
-        return cta_states_close(x, y, I.l);
+        return cta_states_close(x, y, I.l, cta_rhs(P.k));
     };
     if (threadIdx.x == 0) first_s = FWD ? I.nseg : 0;
     __syncthreads();
@@ -220,7 +221,8 @@ __global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, Swee
         for (int b = first; b < I.nseg; ++b) {
             if (b > first && boundary_ok(b)) continue;
             __syncthreads();
-            run_fwd_cta<T, FL>(P, A, make_ctx(P, blockIdx.x, b), sm, RUN_EXACT, snap_ptr<T>(P, I.seg0 + b - 1, 1));
+            run_fwd_cta<T, FL>(P, A, make_ctx(P, blockIdx.x, b), sm, RUN_EXACT, snap_ptr<T>(P, I.seg0 + b - 1, 1),
+                               tier);
             __syncthreads();
             ++fixes;
         }
@@ -228,7 +230,8 @@ __global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, Swee
         for (int b = first; b >= 1; --b) {
             if (b < first && boundary_ok(b)) continue;
             __syncthreads();
-            run_bwd_cta<T, FL>(P, A, make_ctx(P, blockIdx.x, b - 1), sm, RUN_EXACT, snap_ptr<T>(P, I.seg0 + b, 1));
+            run_bwd_cta<T, FL>(P, A, make_ctx(P, blockIdx.x, b - 1), sm, RUN_EXACT, snap_ptr<T>(P, I.seg0 + b, 1),
+                               tier);
             __syncthreads();
             ++fixes;
         }
@@ -239,8 +242,10 @@ __global__ void __launch_bounds__(kCtaThreads) cta_verify_kernel(PlanDev P, Swee
 template <typename T, int K, int FL, bool FWD>
 static cudaError_t launch_wide(const bnd_plan *p, const SweepArgs<T> &A, int32_t t0, int32_t nt, cudaStream_t s) {
     if (nt <= 0) return cudaSuccess;
-    const size_t cta_bytes = sizeof(T) * (size_t)cta_smem_elems(p->max_l);
-    if (cta_fits<T>(p->max_l)) {
+    // block kernels at the highest staging level whose rings fit next to the window
+    const int tier = cta_tier<T>(FWD, FL, p->max_l, cta_rhs(p->k));
+    if (p->wide_cta && tier >= 0) {
+        const size_t cta_bytes = sizeof(T) * (size_t)cta_smem_elems(FWD, FL, p->max_l, cta_rhs(p->k), tier);
         static PerDeviceSlots attr;
         const int ok = per_device(attr, [] {
             return cudaFuncSetAttribute(cta_kernel<T, K, FL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -248,7 +253,8 @@ static cudaError_t launch_wide(const bnd_plan *p, const SweepArgs<T> &A, int32_t
         });
         if (ok <= 0) return cudaErrorInvalidValue;
         const int64_t nch = (int64_t)nt * kWarp;
-        cta_kernel<T, K, FL, FWD><<<(unsigned)nch, kCtaThreads, cta_bytes, s>>>(p->dev, A, (int64_t)t0 * kWarp, nch);
+        cta_kernel<T, K, FL, FWD><<<(unsigned)nch, kCtaThreads, cta_bytes, s>>>(p->dev, A, (int64_t)t0 * kWarp, nch,
+                                                                                tier);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess || !p->wide_segmented) return e;
         static PerDeviceSlots vattr;
@@ -261,7 +267,7 @@ static cudaError_t launch_wide(const bnd_plan *p, const SweepArgs<T> &A, int32_t
         cta_compare_kernel<T, FWD><<<(unsigned)nch, kCtaThreads, 0, s>>>(p->dev, (int64_t)t0 * kWarp, nch);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        cta_verify_kernel<T, K, FL, FWD><<<(unsigned)p->count, kCtaThreads, cta_bytes, s>>>(p->dev, A);
+        cta_verify_kernel<T, K, FL, FWD><<<(unsigned)p->count, kCtaThreads, cta_bytes, s>>>(p->dev, A, tier);
         return cudaGetLastError();
     }
     // windows too large for shared memory: one warp per chain, windows in global memory

@@ -85,16 +85,16 @@ def test_plan_never_splits_when_asked(lib):
 def test_plan_segments_wide_bands_on_the_block_kernels(lib):
     # bandwidths above the register-window limit run on the block kernels, which take
     # segments too (here the asked 1024 rows); without a length, about one segment per
-    # SM (152) over all wide instances, each at least one warm-up long (16 l + 32 rows in
-    # FP32, 48 l + 64 in FP64); seg_len = -1 keeps them whole
+    # SM (152) over all wide instances, each at least one warm-up long (8 l + 32 rows in
+    # FP32, 16 l + 64 in FP64 for wide bands); seg_len = -1 keeps them whole
     p = B.bnd_plan_create(B.BND_F64, _insts([50000, 50000], [12, 3]), 1, dict(seg_len=1024))
     try:
         assert B.bnd_plan_chains(p) == 49 + 49
     finally:
         B.bnd_plan_destroy(p)
-    p = B.bnd_plan_create(B.BND_F64, _insts([200000], [64]), 1)
+    p = B.bnd_plan_create(B.BND_F64, _insts([200000], [128]), 1)
     try:
-        assert B.bnd_plan_chains(p) == round(200000 / (48 * 64 + 64))
+        assert B.bnd_plan_chains(p) == round(200000 / (16 * 128 + 64))
     finally:
         B.bnd_plan_destroy(p)
     p = B.bnd_plan_create(B.BND_F32, _insts([200000], [64]), 1)
@@ -103,6 +103,18 @@ def test_plan_segments_wide_bands_on_the_block_kernels(lib):
     finally:
         B.bnd_plan_destroy(p)
     p = B.bnd_plan_create(B.BND_F64, _insts([50000], [12]), 1, dict(seg_len=-1))
+    try:
+        assert B.bnd_plan_chains(p) == 1
+    finally:
+        B.bnd_plan_destroy(p)
+    # the RHS windows are sized for min(k, 16) columns: FP64 at l = 162 fits a block with one
+    # right-hand side (so it is segmented), not with 16 (one warp per instance, whole)
+    p = B.bnd_plan_create(B.BND_F64, _insts([200000], [162], k=1), 1)
+    try:
+        assert B.bnd_plan_chains(p) > 1
+    finally:
+        B.bnd_plan_destroy(p)
+    p = B.bnd_plan_create(B.BND_F64, _insts([200000], [162], k=16), 16)
     try:
         assert B.bnd_plan_chains(p) == 1
     finally:

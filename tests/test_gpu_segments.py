@@ -247,6 +247,27 @@ def test_wide_bands_segmented(dtype, warm, arr):
         assert_close("Qbar", Qg[c], r["Qbar"], tol["grad"])
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_wide_band_fp64_few_rhs_on_the_block_kernel(k):
+    """The block kernels size their RHS windows for the plan's k: FP64 at l = 160
+    fits one block with up to a few right-hand sides (with 16 it would not).
+    The fused step agrees with the oracle, whole and segmented."""
+    shapes = [(1500, 160)]
+    tol = TOL[B.BND_F64]
+    for tuning in (dict(seg_len=-1), dict(seg_len=400, warmup=16)):
+        insts, lay, plan = setup(shapes, k, B.BND_F64, tuning)
+        got = run_gmm(lay, plan, insts)
+        res, _ = O.batch_step(insts)
+        r = res[0]
+        assert got["info"][0] == 0
+        assert_close("L", lay.unpack_band(got["L"])[0], r["L"], tol["fwd"])
+        assert_close("S", lay.unpack_band(got["S"])[0], r["S"], tol["fwd"])
+        assert_close("X", lay.unpack_rhs(got["X"])[0], r["X"], tol["fwd"])
+        assert_close("Qbar", lay.unpack_band(got["Qb"])[0], r["Qbar"], tol["grad"])
+        assert_close("Bbar", lay.unpack_rhs(got["Bb"])[0], r["Bbar"], tol["grad"])
+        assert abs(got["logdet"][0] - r["logdet"]) <= tol["logdet"] * max(1, abs(r["logdet"]))
+
+
 def run_separate(lay, plan, insts):
     """Forward + backward through the separate operators (any number of RHS):
     C, (L L^T)^{-1} B, I; then the solve, subset-inverse and Cholesky adjoints
