@@ -152,13 +152,21 @@ def algorithmic_bytes(lay, w=4):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gmm_backward_traffic.json")
 
 
+# Sources of the kernels the uneven batch runs (register-window sweeps, staged
+# I/O, reruns, verify, plan and entry points); the wide-band block kernels,
+# the one-warp fallback, the products and the allocation-free solve are not
+# among them.
+HOT_SOURCES = ("common.cuh", "sweep_impl.cuh", "sweep_io.cuh", "sweep_staged.cuh", "sweep_launch.cuh", "plan.cu",
+               "abi.cu", "sweep_fwd_float.cu", "sweep_bwd_float.cu") + tuple(f"sweep_staged_l{i}.cu" for i in range(1, 9))
+
+
 def source_hash():
-    """Hash of the CUDA sources and the C header: a stored DRAM traffic figure
-    is only reported while the kernels it was measured on are unchanged."""
-    import glob
+    """Hash of the sources of the uneven batch's kernels and the C header: a
+    stored DRAM traffic figure is only reported while the kernels it was
+    measured on are unchanged."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1902_10078_gb300", "csrc", "*.cu*")))
+    files = [os.path.join(ROOT, "paper_1902_10078_gb300", "csrc", f) for f in sorted(HOT_SOURCES)]
     files.append(os.path.join(ROOT, "include", "banded.h"))
     for f in files:
         h.update(os.path.basename(f).encode())

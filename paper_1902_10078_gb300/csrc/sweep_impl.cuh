@@ -78,9 +78,41 @@ template <> struct Num<float> {
     static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 };
+// FP64 reciprocal and reciprocal square root of the per-row critical path.
+// FP64 arithmetic on this part is slow (about 64 cycles per dependent FMA), so
+// instead of the IEEE division and the library rsqrt these take the FP32
+// hardware estimate (relative error below 2^-22) and refine it with two
+// Newton-Raphson steps, each of which about squares the relative error
+// (2^-44, then below the FP64 rounding unit): accurate to about one ulp, not
+// correctly rounded, and without branches inside the FP32 exponent range
+// (outside it, and for zero, negative or non-finite arguments, the IEEE
+// operation is used).
+//   1/x:       r <- r + r (1 - x r)
+//   1/sqrt(x): r <- r + (r / 2) (1 - x r^2)
+__device__ __forceinline__ double rcp_newton(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)x));
+    double r = (double)rf;
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    if (!(x > 1e-36 && x < 1e36)) return rsqrt(x);
+    float rf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)x));
+    double r = (double)rf;
+    double e = fma(-x * r, r, 1.0);
+    r = fma(0.5 * r, e, r);
+    e = fma(-x * r, r, 1.0);
+    return fma(0.5 * r, e, r);
+}
 template <> struct Num<double> {
-    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt_newton(x); }
+    static __device__ __forceinline__ double rcp(double x) { return rcp_newton(x); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 };
 
@@ -145,10 +177,28 @@ __device__ __forceinline__ bool inb(int64_t x, int64_t n) { return !CHECK || x <
 // (Kahan) float sum, converted to double once per chain, which keeps FP64
 // arithmetic (slow on this part) off the per-row path.
 template <typename T> struct LogSum;
+// FP64: the running product of the pivots kept as m 2^e with m in [0.5, 1) (one
+// multiplication and a few integer operations per row), and one logarithm at
+// the end: a logarithm per row costs some 40 FP64 operations on this part's
+// slow FP64 pipe.  Each row rounds the product once, so the relative error of
+// the product after n rows is below n 2^-53 (an absolute error below n 2^-53
+// in the log-det).  Pivots whose product leaves the normal range (or that are
+// not positive: the factorization has failed then) go to a plain sum of
+// logarithms instead.
 template <> struct LogSum<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double piv) { s += log(piv); }
-    __device__ __forceinline__ double value() const { return s; }
+    double m = 1.0, slow = 0.0;
+    long long e = 0;
+    __device__ __forceinline__ void add(double piv) {
+        const double p = m * piv;
+        if (p >= 2.2250738585072014e-308 && p <= 1.7976931348623157e308) {
+            const long long b = __double_as_longlong(p);
+            e += ((b >> 52) & 0x7ff) - 1022;
+            m = __longlong_as_double((b & ~(0x7ffLL << 52)) | (1022LL << 52));
+        } else {
+            slow += log(piv);
+        }
+    }
+    __device__ __forceinline__ double value() const { return log(m) + (double)e * 0.6931471805599453 + slow; }
 };
 template <> struct LogSum<float> {
     float s = 0.0f, comp = 0.0f;
@@ -168,7 +218,7 @@ enum : int { RUN_COLD = 0, RUN_EXACT = 1 };
 // body is instantiated once per row of the tile); wider bands keep one copy of
 // the body, whose size otherwise overflows the instruction cache.
 #ifndef BND_INTERIOR_UNROLL_MAX_L
-#define BND_INTERIOR_UNROLL_MAX_L 8
+#define BND_INTERIOR_UNROLL_MAX_L 4
 #endif
 
 // ===========================================================================
