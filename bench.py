@@ -401,7 +401,11 @@ def run_ours(args, rank, world, device_index):
 
     # kernels per step: 4 sweeps x (one kernel per bandwidth class present + the verify pass when segmented)
     classes = len(set(int(l) if 1 <= int(l) <= 8 else 0 for l in lay.ls))
-    launches_per_step = 4 * (classes + (1 if plan.chains > count else 0))
+    # (a segmented plan adds, per bandwidth class, the mark kernel and the staged rerun pass, and
+    # one verify kernel per sweep: the launch list of profiles/ shows 64 kernels per step here)
+    segmented = plan.chains > count
+    reruns = segmented and not (int(tuning.get("flags") or 0) & 4)
+    launches_per_step = 4 * (classes * (3 if reruns else 1) + (1 if segmented else 0))
     fwd_b, bwd_b, floor_b = algorithmic_bytes(lay)
     return dict(lay=lay, plan=plan, ms=ms, ms_e2e=ms_e2e, ms_fwd=ms_fwd, ms_bwd=ms_bwd, entries=entries,
                 entries_all=entries_all,

@@ -131,14 +131,12 @@ __device__ __forceinline__ T cta_block_sum(T v, T *red) {
 // meet in log2 G shuffles.  Every thread of the block must call it.
 template <typename T, class F, class Out>
 __device__ __forceinline__ void cta_rows_reduce(int nt, int nq, F f, Out out) {
-    const int cap = nt > 0 ? kCtaThreads / nt : kWarp;
-    const int lg = cap >= 32 ? 5 : cap >= 16 ? 4 : cap >= 8 ? 3 : cap >= 4 ? 2 : cap >= 2 ? 1 : 0;
-    const int G = 1 << lg;
-    const int per_pass = kCtaThreads >> lg;
-    const int g = (int)threadIdx.x & (G - 1);
-    const int tq = (int)threadIdx.x >> lg;
+    int G = kWarp;
+    while (G > 1 && nt * G > kCtaThreads) G >>= 1;
+    const int per_pass = kCtaThreads / G;
+    const int g = (int)threadIdx.x % G;
     for (int t0 = 1; t0 <= nt; t0 += per_pass) {
-        const int t = t0 + tq;
+        const int t = t0 + (int)threadIdx.x / G;
         T acc = T(0);
         if (t <= nt)
             for (int q = 1 + g; q <= nq; q += G) acc = f(t, q, acc);
@@ -311,9 +309,6 @@ struct CtaStream {
     int ahead, behind;
     T *ring;             // nullptr: direct
     int rs, nslot, cur;
-    int64_t ipos;        // next position to issue, and its slot
-    int islot;
-    int t_dq, t_e, s_dq, s_e;   // this thread's first (column, element) of a copy batch and its stride
 
     // Returns the shared memory after the ring (unchanged when direct or absent).
     __device__ T *setup(const T *g_, int64_t stride_, int64_t cs_, int rows_, int rows_cap, bool band_, int ahead_,
@@ -323,38 +318,29 @@ struct CtaStream {
         rs = cta_even(rows_cap);
         nslot = ahead + behind + 2 * kCtaTile;
         cur = 0;
-        ipos = -(int64_t)behind;
-        islot = behind > 0 ? nslot - behind : 0;
-        const int r = rows > 0 ? rows : 1;
-        t_dq = (int)threadIdx.x / r; t_e = (int)threadIdx.x - t_dq * r;
-        s_dq = kCtaThreads / r; s_e = kCtaThreads - s_dq * r;
         ring = (staged && g) ? mem : nullptr;
         return ring ? mem + (int64_t)nslot * rs : mem;
     }
     __device__ __forceinline__ bool inside(int64_t c, int e) const { return c >= 0 && c < n && (!band || c + e < n); }
-    // copies of the next `ncols` positions (at most nslot of them)
-    __device__ void issue(int ncols) {
+    // copies of positions [q0, q1] (at most nslot of them)
+    __device__ void issue(int64_t q0, int64_t q1) {
         if (!ring || rows <= 0) return;
-        const int64_t c0 = jfirst + (int64_t)dir * ipos;
-        int dq = t_dq, e = t_e;
-        while (dq < ncols) {
-            const int64_t c = c0 + (dir > 0 ? dq : -dq);
+        const int cnt = (int)(q1 - q0 + 1) * rows;
+        int s0 = (int)(q0 % nslot);
+        if (s0 < 0) s0 += nslot;
+        for (int x = threadIdx.x; x < cnt; x += kCtaThreads) {
+            const int dq = x / rows, e = x - dq * rows;
+            const int64_t c = jfirst + (int64_t)dir * (q0 + dq);
             const bool ok = inside(c, e);
-            int sl = islot + dq;
+            int sl = s0 + dq;
             if (sl >= nslot) sl -= nslot;
             cp_async_elem(ring + sl * rs + e, ok ? g + e * stride + c * cs : g, ok);
-            dq += s_dq;
-            e += s_e;
-            if (e >= rows) { e -= rows; ++dq; }
         }
-        ipos += ncols;
-        islot += ncols;
-        if (islot >= nslot) islot -= nslot;
     }
-    // the positions the first tile needs (its rows' whole span: behind + kCtaTile + ahead), then
-    // kCtaTile more per tile (they enter `ahead` positions in front of the tile)
-    __device__ void issue_first() { issue(behind + kCtaTile + ahead); }
-    __device__ void issue_next() { issue(kCtaTile); }
+    // the positions the first tile needs (its rows' whole span); a later tile starting at q0
+    // adds the ones that enter `ahead` positions in front of it
+    __device__ void issue_first() { issue(-(int64_t)behind, (int64_t)kCtaTile - 1 + ahead); }
+    __device__ void issue_next(int64_t q0) { issue(q0 + ahead, q0 + kCtaTile - 1 + ahead); }
     __device__ __forceinline__ T at(int e, int o) const {
         if (ring) return ring[wrap_slot(cur + o, nslot) * rs + e];
         const int64_t c = jc + (int64_t)dir * o;
@@ -543,7 +529,7 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         CtaStream<T> *st[4] = {&sQ, &sB, &sSb, &sS};
         for (CtaStream<T> *x : st) {
             if (q0 == 0) x->issue_first();
-            else x->issue_next();
+            else x->issue_next(q0);
         }
     };
     auto advance = [&] {
@@ -745,7 +731,7 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         CtaStream<T> *st[5] = {&sL, &sB, &sLb, &sLw, &sX};
         for (CtaStream<T> *x : st) {
             if (q0 == 0) x->issue_first();
-            else x->issue_next();
+            else x->issue_next(q0);
         }
     };
     auto advance = [&] {
