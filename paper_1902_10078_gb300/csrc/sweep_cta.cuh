@@ -145,39 +145,6 @@ __device__ __forceinline__ void cta_rows_reduce(int nt, int nq, F f, Out out) {
     }
 }
 
-// The pairs (x, y), 1 <= y <= x <= l, of a triangle folded into a rectangle of
-// ceil(l/2) rows of l + 1 entries: rectangle row i holds triangle row i
-// (entries 0..i) followed by triangle row l-1-i, so the rectangle has no holes
-// (odd l: the last rectangle row is half padding).  Thread t visits entries
-// t, t + kCtaThreads, ... without divisions inside the loop.
-struct FoldIter {
-    int l, lw, i, b, di, db, np, p;
-    __device__ FoldIter(int l_, int tid) : l(l_), lw(l_ + 1) {
-        np = ((l + 1) / 2) * lw;
-        p = tid;
-        i = tid / lw;
-        b = tid - i * lw;
-        di = kCtaThreads / lw;
-        db = kCtaThreads - di * lw;
-    }
-    __device__ __forceinline__ bool valid() const { return p < np; }
-    __device__ __forceinline__ bool pair(int &x, int &y) const {
-        int xr, yr;
-        bool ok;
-        if (b <= i) { xr = i; yr = b; ok = xr < l; }
-        else { xr = l - 1 - i; yr = b - i - 1; ok = xr > i; }   // odd l: the middle row appears once
-        x = xr + 1;
-        y = yr + 1;
-        return ok;
-    }
-    __device__ __forceinline__ void next() {
-        p += kCtaThreads;
-        i += di;
-        b += db;
-        if (b >= lw) { b -= lw; ++i; }
-    }
-};
-
 __device__ __forceinline__ int wrap_slot(int s, int lw) { return s >= lw ? s - lw : (s < 0 ? s + lw : s); }
 
 // Save (or load) the state of a block sweep whose current column has slot sj:
@@ -346,6 +313,16 @@ struct CtaStream {
         const int64_t c = jc + (int64_t)dir * o;
         return (g && inside(c, e)) ? g[e * stride + c * cs] : T(0);
     }
+    // The column o positions ahead: element e at p[e * step] (no zero fill: the caller stays
+    // inside the band and the matrix).
+    __device__ __forceinline__ const T *col(int o, int64_t &step) const {
+        if (ring) {
+            step = 1;
+            return ring + wrap_slot(cur + o, nslot) * rs;
+        }
+        step = stride;
+        return g + (jc + (int64_t)dir * o) * cs;
+    }
     __device__ __forceinline__ void advance() {
         jc += dir;
         if (ring) cur = wrap_slot(cur + 1, nslot);
@@ -414,7 +391,6 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
     int32_t info = 0;
     int sj = (int)(j0 % lw);                     // slot of column j: j mod (l + 1)
     if (mode == RUN_EXACT && exact) cta_state_io(W, U, l, km, sj, const_cast<T *>(exact), false);
-    const FoldIter fold0(l, tid);                // this thread's pairs of the window update
     auto row = [&](int64_t q) {
         const int64_t j = j0 + q;
         const bool out = j >= c.a;                // warm-up rows only carry the state
@@ -470,12 +446,12 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         __syncthreads();
         // ---- phase C: window update
         if (CHOL) {
-            // S(j+x, j+y) += L[j+x, j] L[j+y, j], 1 <= y <= x <= l
-            for (FoldIter it = fold0; it.valid(); it.next()) {
-                int x, y;
-                if (!it.pair(x, y)) continue;
-                const int ix = wrap_slot(sj + y, lw) * rs + (x - y);
-                W[ix] = fma(lc[x], lc[y], W[ix]);
+            // S(j+x, j+y) += L[j+x, j] L[j+y, j], 1 <= y <= x <= l: warp w takes the window columns
+            // j+y, y = w+1, w+1+kCtaWarps, ..., its lanes the entries f = x - y of a column
+            for (int y = 1 + warp; y <= l; y += kCtaWarps) {
+                const T ly = lc[y];
+                T *col = W + wrap_slot(sj + y, lw) * rs;
+                for (int f = lane; f <= l - y; f += kWarp) col[f] = fma(lc[y + f], ly, col[f]);
             }
         }
         if (SOLVE) {
@@ -503,15 +479,17 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
                     }
                     part = fma(v, lc[t], part);
                 });
-            // pair adjoints: pend(i+t, i+q) -= b[q] U[t] (+ b[t] U[q] for t != q)
-            for (FoldIter it = fold0; it.valid(); it.next()) {
-                int x, y;
-                if (!it.pair(x, y)) continue;
-                const int ix = wrap_slot(sj + y, lw) * rs + (x - y);
-                T v = W[ix];
-                v = fma(-av[x], uv[y], v);
-                if (x != y) v = fma(-av[y], uv[x], v);
-                W[ix] = v;
+            // pair adjoints: pend(i+x, i+y) -= b[x] U[y] (+ b[y] U[x] for x != y), 1 <= y <= x <= l,
+            // columns y over the warps and entries f = x - y over the lanes as above
+            for (int y = 1 + warp; y <= l; y += kCtaWarps) {
+                const T ay = av[y], uy = uv[y];
+                T *col = W + wrap_slot(sj + y, lw) * rs;
+                for (int f = lane; f <= l - y; f += kWarp) {
+                    T v = col[f];
+                    v = fma(-av[y + f], uy, v);
+                    if (f) v = fma(-ay, uv[y + f], v);
+                    col[f] = v;
+                }
             }
             // diagonal of L-bar: -2 b0 / L_ii^3 - (sum_t bU[t] L[i+t, i]) / L_ii^2
             const T s = cta_block_sum(part, red);
@@ -606,9 +584,6 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
     const T two_ldbar = (ALG2 && A.ldbar) ? T(2.0 * A.ldbar[c.inst]) : T(0);
     int sj = (int)(j0 % lw);                     // slot of column j: j mod (l + 1)
     if (mode == RUN_EXACT && exact) cta_state_io(W, U, l, km, sj, const_cast<T *>(exact), false);
-    // L[j + f, j - e] (0 <= f, 1 <= e <= l, f + e <= l): entry f + e of column j - e, e positions
-    // ahead in the backward sweep
-    auto lwin = [&](int e, int f) -> T { return sLw.at(f + e, e); };
     auto row = [&](int64_t q) {
         const int64_t j = j0 - q;
         const bool out = j < c.b;                 // warm-up rows only carry the state
@@ -674,17 +649,23 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         if (SOLVE && tid < kk) U[tid * lw + sj] = sc[tid];      // x_j enters the ring
         if (ALG2) {
             // column j of L-bar: outer terms, log-det term, then Alg. 2 (off-diagonals first)
+            if (OUTER) {
+                // rw[d] -= sum_r X[j+d, r] ybar_r + x_{j+d, r} y_r (x_j itself is still in sc), lane
+                // groups over d
+                cta_rows_reduce<T>(
+                    l + 1, kk,
+                    [&](int t, int q, T acc) {
+                        const int d = t - 1, r = q - 1;
+                        const T bb = d == 0 ? sc[r] : U[r * lw + wrap_slot(sj + d, lw)];
+                        acc = fma(sX.at(r, -d), sc[2 * kCtaMaxK + r], acc);
+                        return fma(bb, sc[kCtaMaxK + r], acc);
+                    },
+                    [&](int t, T acc) { rw[t - 1] -= acc; });
+                __syncthreads();
+            }
             T part = T(0);
             for (int d = tid; d <= l; d += kCtaThreads) {
                 T v = rw[d];
-                if (OUTER) {
-                    for (int r = 0; r < kk; ++r) {
-                        const T ybar = sc[2 * kCtaMaxK + r], y = sc[kCtaMaxK + r];
-                        const T bb = d == 0 ? sc[r] : U[r * lw + wrap_slot(sj + d, lw)];
-                        v = fma(-sX.at(r, -d), ybar, v);
-                        v = fma(-bb, y, v);
-                    }
-                }
                 if (d == 0) {
                     v = fma(two_ldbar, rinv, v);
                     rw[0] = v;
@@ -703,20 +684,31 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
             }
             // pending L-bar of the window columns m = j - e, e = 1..nm: L[j+d, m] gets -Qb[d] L[j, m]
             // (d >= 1, d + e <= l); L[j, m] gets -2 Qb[0] L[j, m] - sum_d Qb[d] L[j+d, m]
+            // (G lanes of a warp per column, as in cta_rows_reduce, with the column's pointers and
+            // L[j, m] held across the lane's terms)
             const int nm = (int)imin64((int64_t)l, j);
-            cta_rows_reduce<T>(
-                nm, dmax,
-                [&](int e, int d, T acc) {
-                    if (d > l - e) return acc;                     // L[j+d, j-e] is outside the band
-                    const T qb = rw[d];
-                    const int ix = wrap_slot(sj - e, lw) * rs + d + e;
-                    W[ix] = fma(-qb, lwin(e, 0), W[ix]);
-                    return fma(qb, lwin(e, d), acc);
-                },
-                [&](int e, T acc) {
-                    const int ix = wrap_slot(sj - e, lw) * rs + e;
-                    W[ix] = W[ix] - T(2) * qb0 * lwin(e, 0) - acc;
-                });
+            int G = kWarp;
+            while (G > 1 && nm * G > kCtaThreads) G >>= 1;
+            const int per_pass = kCtaThreads / G, g = tid % G;
+            for (int e0 = 1; e0 <= nm; e0 += per_pass) {
+                const int e = e0 + tid / G;
+                T acc = T(0), ljm = T(0);
+                T *wc = W;
+                if (e <= nm) {
+                    int64_t st;
+                    const T *lcol = sLw.col(e, st);               // column m = j - e of L
+                    wc = W + wrap_slot(sj - e, lw) * rs;           // its pending L-bar
+                    ljm = lcol[e * st];                            // L[j, m]
+                    const int dl = dmax < l - e ? dmax : l - e;              // L[j+d, m] inside the band
+                    for (int d = 1 + g; d <= dl; d += G) {
+                        const T qb = rw[d];
+                        wc[d + e] = fma(-qb, ljm, wc[d + e]);
+                        acc = fma(qb, lcol[(d + e) * st], acc);
+                    }
+                }
+                for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (g == 0 && e <= nm) wc[e] = wc[e] - T(2) * qb0 * ljm - acc;
+            }
         }
         __syncthreads();
         // column j + l leaves the TAKA window and the x ring (row j - 1 reads columns j ..
