@@ -363,41 +363,63 @@ def run_ours(args, rank, world, device_index):
     out_keys = ("X", "S", "Qbar", "Bbar", "logdet", "info")
     back = [{k: torch.empty(st["out"][k].shape, dtype=st["out"][k].dtype).pin_memory() for k in out_keys}
             for st in sets]
-    s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in sets]
+    ncs = max(1, args.copy_streams)                     # copy streams per direction
+    s_in = [torch.cuda.Stream() for _ in range(ncs)]
+    s_out = [torch.cuda.Stream() for _ in range(ncs)]
+    s_comp = torch.cuda.Stream()
+    ev_in = [[torch.cuda.Event() for _ in range(ncs)] for _ in sets]
     ev_comp = [torch.cuda.Event() for _ in sets]
-    ev_out = [torch.cuda.Event() for _ in sets]
+    ev_out = [[torch.cuda.Event() for _ in range(ncs)] for _ in sets]
+
+    def pieces(dst, src):
+        """Contiguous pieces of a copy, one per copy stream."""
+        d, s_ = dst.view(-1), src.view(-1)
+        step_ = (d.numel() + ncs - 1) // ncs
+        return [(d[o:o + step_], s_[o:o + step_]) for o in range(0, d.numel(), step_)]
 
     def e2e_steps(count):
         for i in range(count):
             b = i % 2
             st = sets[b]
-            s_in.wait_event(ev_comp[b])                 # the step that last read these inputs is done
-            with torch.cuda.stream(s_in):
-                for k in in_keys:
-                    st["dev"][k].copy_(pinned[k], non_blocking=True)
-                ev_in[b].record(s_in)
-            s_comp.wait_event(ev_in[b])
-            s_comp.wait_event(ev_out[b])                # this set's previous results are out
+            for c, sc in enumerate(s_in):
+                sc.wait_event(ev_comp[b])               # the step that last read these inputs is done
+                with torch.cuda.stream(sc):
+                    for k in in_keys:
+                        for p_i, (dd, ss) in enumerate(pieces(st["dev"][k], pinned[k])):
+                            if p_i == c:
+                                dd.copy_(ss, non_blocking=True)
+                    ev_in[b][c].record(sc)
+            for c in range(ncs):
+                s_comp.wait_event(ev_in[b][c])
+                s_comp.wait_event(ev_out[b][c])         # this set's previous results are out
             with torch.cuda.stream(s_comp):
                 d, o = st["dev"], st["out"]
                 B.banded_gmm_forward(plan.handle, d["Q"], d["B"], o["L"], o["X"], o["S"], o["logdet"], o["info"])
                 B.banded_gmm_backward(plan.handle, o["L"], o["X"], o["S"], d["Xbar"], d["Sbar"], ldbar, o["Qbar"],
                                       o["Bbar"])
                 ev_comp[b].record(s_comp)
-            s_out.wait_event(ev_comp[b])
-            with torch.cuda.stream(s_out):
-                for k in out_keys:
-                    back[b][k].copy_(st["out"][k], non_blocking=True)
-                ev_out[b].record(s_out)
+            for c, sc in enumerate(s_out):
+                sc.wait_event(ev_comp[b])
+                with torch.cuda.stream(sc):
+                    for k in out_keys:
+                        for p_i, (dd, ss) in enumerate(pieces(back[b][k], st["out"][k])):
+                            if p_i == c:
+                                dd.copy_(ss, non_blocking=True)
+                    ev_out[b][c].record(sc)
 
     e2e_steps(2)
     torch.cuda.synchronize()
     e_reps = max(4, min(args.steps, 10))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(s_in)
+    torch.cuda.synchronize()
+    a.record(s_in[0])
+    for sc in s_in[1:] + [s_comp] + s_out:
+        sc.wait_event(a)                                # nothing of the timed steps starts before a
     e2e_steps(e_reps)
-    b.record(s_out)
+    for evs in ev_out:                                  # b after every result copy
+        for ev in evs:
+            s_comp.wait_event(ev)
+    b.record(s_comp)
     torch.cuda.synchronize()
     ms_e2e = a.elapsed_time(b) / e_reps
     h2d = sum(pinned[k].numel() * pinned[k].element_size() for k in in_keys)
@@ -747,6 +769,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--k", type=int, default=4)
+    ap.add_argument("--copy-streams", type=int, default=1, help="end-to-end: copy streams per direction")
     ap.add_argument("--seg-len", type=int, default=0, help="rows per segment (0: the library default)")
     ap.add_argument("--warm", type=int, default=0, help="warm-up rows (0: per-bandwidth default)")
     ap.add_argument("--flags", type=int, default=0, help="plan tuning flags (see bnd_tuning)")

@@ -426,13 +426,11 @@ __device__ void run_fwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
         } else {
             rinv = Num<T>::rcp(lc[0]);
         }
-        if (SOLVE) {
-            __syncthreads();                      // lc complete (CHOL) before the RHS rows use it
-            if (tid < kk) {
-                const T y = yv[tid] * rinv;
-                yv[tid] = y;
-                if (out) Xo[(int64_t)(A.rhs0 + tid) * c.ldr + j * cs] = y;
-            }
+        if (SOLVE && tid < kk) {
+            // y_r needs only the pivot; the column of L is read after the barrier below
+            const T y = yv[tid] * rinv;
+            yv[tid] = y;
+            if (out) Xo[(int64_t)(A.rhs0 + tid) * c.ldr + j * cs] = y;
         }
         if (ALG4) {
             const T b0 = av[0];
