@@ -106,9 +106,11 @@ typedef struct {
 typedef struct {
     int64_t seg_len;     /* rows per chain segment; long instances are split into segments
                             run in parallel (0 = default: 2048 for rows, 384 for panels;
-                            < 0 = never split) */
+                            bandwidths above 8: about 152 segments over the plan's wide
+                            instances, each at least one warm-up long; < 0 = never split) */
     int32_t warmup;      /* warm-up rows of a speculative segment start (0 = default:
-                            16 l + 32 rows in FP32, 48 l + 64 in FP64) */
+                            16 l + 32 rows in FP32, 48 l + 64 in FP64; bandwidths above 8:
+                            8 l + 32 and 16 l + 64) */
     int32_t blocks_per_sm; /* persistent-grid occupancy (0 = default) */
     int32_t flags;       /* bit 0: never use the shared-memory staged kernels;
                             bit 1: segment length seg_len * warmup / 128 (the same share of
@@ -128,10 +130,15 @@ typedef struct bnd_plan bnd_plan;
  * into row segments ("chains") that run as independent lanes of the GPU;
  * chains of equal bandwidth are grouped 32 to a warp; warp tasks are ordered
  * longest first for the persistent kernels.  Segments of one instance start
- * from a speculative warm-up and are checked bit for bit against their
- * neighbour afterwards; a mismatch reruns that segment from its exact start
- * state, so results never depend on the segmentation beyond rounding of the
- * warm-up (which the check excludes).
+ * from a speculative warm-up and are checked against their neighbour
+ * afterwards; a mismatch reruns that segment from its exact start state.  For
+ * bandwidths up to 8 the check is bit for bit, so results do not depend on the
+ * segmentation.  Above 8 (one thread block per segment) a start passes when
+ * its state agrees with the exact one within 2^-16 (FP32) / 2^-44 (FP64) of
+ * the largest entry of each part of the state (band window; each RHS row):
+ * there a converged cold start stays about one ulp from the exact state
+ * instead of meeting it, so results agree with an unsplit run to rounding
+ * noise (deterministically for a given plan).
  *
  * bnd_plan_create copies `inst` (HOST) and returns BND_EINVAL on a bad
  * descriptor (n < 1, l < 0 or > 1024, cs < 0, ld < n cs, ldr < n cs when
