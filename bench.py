@@ -160,8 +160,17 @@ HOT_SOURCES = ("common.cuh", "sweep_impl.cuh", "sweep_io.cuh", "sweep_staged.cuh
                "abi.cu", "sweep_fwd_float.cu", "sweep_bwd_float.cu") + tuple(f"sweep_staged_l{i}.cu" for i in range(1, 9))
 
 
+def _code_only(text):
+    """C/C++ source without its comments and blank-line differences (a comment
+    edit does not change a kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def source_hash():
-    """Hash of the sources of the uneven batch's kernels and the C header: a
+    """Hash of the code of the uneven batch's kernels and the C header: a
     stored DRAM traffic figure is only reported while the kernels it was
     measured on are unchanged."""
     import hashlib
@@ -170,8 +179,8 @@ def source_hash():
     files.append(os.path.join(ROOT, "include", "banded.h"))
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
