@@ -322,6 +322,7 @@ def run_ours(args, rank, world, device_index):
         print(json.dumps({"profile_once": True, "band_entries": entries}), flush=True)
         return None
     fixups = sum(B.bnd_plan_fixups(plan.handle, kk) for kk in range(6))
+    assert B.bnd_plan_fixups(plan.handle, 6) == 0, "a bounded device wait gave up"
 
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):

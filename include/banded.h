@@ -168,8 +168,11 @@ int32_t bnd_plan_layout(const bnd_plan *plan);
 /* Number of segments rerun by the verify pass of the last launch of the given
  * sweep kind (0 = Cholesky forward sweep, 1 = subset-inverse sweep,
  * 2 = subset-inverse adjoint sweep, 3 = Cholesky adjoint sweep, 4 = forward
- * solve sweep, 5 = backward solve sweep).  Copies the counter into the HOST
- * int64 *out and synchronises `stream`.  Diagnostic only. */
+ * solve sweep, 5 = backward solve sweep).  kind = 6 returns instead the number
+ * of bounded device waits (on the shared-memory barriers of the bulk tile
+ * copies, a build option) that gave up since the plan was bound: it must be 0;
+ * any other value means the results of the plan's calls are invalid.  Copies
+ * the counter into the HOST int64 *out and synchronises `stream`. */
 bnd_status bnd_plan_fixups(const bnd_plan *plan, int32_t kind, int64_t *out, void *stream);
 
 /* ---------------------------------------------------------------------------

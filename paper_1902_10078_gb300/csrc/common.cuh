@@ -51,6 +51,10 @@ constexpr int kPanelLanes = 32;    // column stride of a panel group
 // Sweep kinds (for state snapshots and fixup counters).
 enum SweepKind : int32_t { kSweepChol = 0, kSweepTaka = 1, kSweepTakaBar = 2, kSweepCholBar = 3,
                            kSweepFSolve = 4, kSweepBSolve = 5, kNumSweepKinds = 6 };
+// Plan counters: task queue heads [0, kinds), fixup counts [kinds, 2 kinds),
+// then the count of bounded device waits that gave up (must stay 0).
+constexpr int kTimeoutCounter = 2 * kNumSweepKinds;
+constexpr int kNumCounters = 2 * kNumSweepKinds + 1;
 
 // Device view of a bound plan.
 struct PlanDev {
@@ -69,7 +73,7 @@ struct PlanDev {
     int32_t warm;
     // workspace areas
     int64_t nsegs;
-    uint32_t *counters;      // [2 * kNumSweepKinds]: task queue heads, then fixup counters
+    uint32_t *counters;      // [kNumCounters]: task queue heads, fixup counters, wait timeouts
     void *snap;              // per segment: 2 snapshots (start, end) of snap_words elements
     int64_t snap_words;
     double *seg_logdet;      // per segment partial log-det

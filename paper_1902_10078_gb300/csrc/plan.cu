@@ -406,7 +406,7 @@ extern "C" bnd_status bnd_plan_create(bnd_plan **out, bnd_dtype dtype, int32_t c
     p->off_tasks = take(sizeof(Task) * (size_t)p->ntasks);
     p->off_tiles = take(sizeof(int64_t) * ((size_t)std::max(count, p->ngroups) + 1));
     p->off_groups = take(sizeof(int32_t) * ((size_t)p->ngroups + 1));
-    p->off_counters = take(sizeof(unsigned int) * 2 * kNumSweepKinds);
+    p->off_counters = take(sizeof(unsigned int) * kNumCounters);
     p->off_snap = take(esz * (size_t)nsegs * 2 * (size_t)p->snap_words);
     p->off_logdet = take(sizeof(double) * (size_t)nsegs);
     p->off_info = take(sizeof(int32_t) * (size_t)nsegs);
@@ -485,7 +485,7 @@ extern "C" bnd_status bnd_plan_bind(bnd_plan *p, void *ws, size_t ws_bytes, void
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + p->off_tiles, p->tile_prefix, sizeof(int64_t) * ntab, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && p->ngroups > 0)
         e = cudaMemcpyAsync(base + p->off_groups, p->group_first, sizeof(int32_t) * ((size_t)p->ngroups + 1), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + p->off_counters, 0, sizeof(unsigned int) * 2 * kNumSweepKinds, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + p->off_counters, 0, sizeof(unsigned int) * kNumCounters, s);
     if (e == cudaSuccess && p->nsegs)
         e = cudaMemcpyAsync(base + p->off_seg_chain, p->seg_chain, sizeof(int32_t) * (size_t)p->nsegs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + p->off_rerun_cnt, 0, sizeof(uint32_t) * (kRegMaxL + 1), s);
@@ -517,9 +517,10 @@ extern "C" void bnd_plan_destroy(bnd_plan *p) {
 }
 
 extern "C" bnd_status bnd_plan_fixups(const bnd_plan *p, int32_t kind, int64_t *out, void *stream) {
-    if (!p || !p->bound || !out || kind < 0 || kind >= kNumSweepKinds) return BND_EINVAL;
+    if (!p || !p->bound || !out || kind < 0 || kind > kNumSweepKinds) return BND_EINVAL;
     unsigned int v = 0;
-    cudaError_t e = cudaMemcpyAsync(&v, p->dev.counters + kNumSweepKinds + kind, sizeof(v), cudaMemcpyDeviceToHost,
+    const int slot = kind == kNumSweepKinds ? kTimeoutCounter : kNumSweepKinds + kind;
+    cudaError_t e = cudaMemcpyAsync(&v, p->dev.counters + slot, sizeof(v), cudaMemcpyDeviceToHost,
                                     (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return BND_ECUDA;

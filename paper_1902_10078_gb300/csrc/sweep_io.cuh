@@ -69,6 +69,35 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// Shared-memory barriers and bulk copies (the bulk-copy panel I/O, a build
+// option): one thread arms a barrier with the bytes it expects and issues
+// whole-block copies from global memory that complete on it; readers wait for
+// the barrier's phase with a bounded number of polls.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// 16-byte aligned source and destination, size a multiple of 16 bytes; completes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+// Polls of a barrier wait before it gives up (counted in the plan's timeout counter).
+constexpr uint32_t kBulkSpinLimit = 1u << 24;
+
 template <typename T> struct SweepArgs;
 
 // ---------------------------------------------------------------------------
@@ -290,7 +319,7 @@ struct StagedIO {
 // the warp (the copies are cooperative); lanes outside their own rows skip
 // the steps.
 // ---------------------------------------------------------------------------
-template <typename T, class SW, int R, int DIR>
+template <typename T, class SW, int R, int DIR, bool BULK = false>
 struct PanelIO {
     static constexpr int NIN = SW::NIN;
     static constexpr int NOUT = SW::NOUT;
@@ -299,7 +328,9 @@ struct PanelIO {
     static constexpr int kPieces = kTileElems * (int)sizeof(T) / (16 * kWarp);   // 16-byte pieces per lane
     static constexpr int kPieceElems = 16 / (int)sizeof(T);
     static constexpr int kRingElems = NIN * R * kTileElems;
-    static constexpr int kWarpElems = kRingElems;
+    // BULK: one shared-memory barrier per ring slot after the ring
+    static constexpr int kBarElems = BULK ? (R * 8 + (int)sizeof(T) - 1) / (int)sizeof(T) : 0;
+    static constexpr int kWarpElems = kRingElems + kBarElems;
     static constexpr bool kWarpUniform = true;
     static_assert(kPieces >= 1, "a tile must give every lane at least one 16-byte piece");
 
@@ -330,9 +361,15 @@ struct PanelIO {
     int lane;
     int cR, iR;                     // ring slots of the current row tile and of the next one to issue
     const T *cur;                   // this lane's column in the current slot
+    uint64_t *bars;                 // BULK: barrier of each slot
+    uint32_t par;                   // BULK: parity of the next phase to wait for, bit q for slot q
+    uint32_t *err;                  // BULK: count of waits that gave up
+    bool bulk_ok;                   // BULK: every input stream active (whole blocks can be copied)
 
-    __device__ PanelIO(const ChainPtrs<T> &p, const SweepArgs<T> &A, const Task &g, T *warp_smem, int lane_)
-        : ring(warp_smem), lane(lane_) {
+    __device__ PanelIO(const ChainPtrs<T> &p, const SweepArgs<T> &A, const Task &g, T *warp_smem, int lane_,
+                       uint32_t *err_ = nullptr)
+        : ring(warp_smem), lane(lane_), bars(reinterpret_cast<uint64_t *>(warp_smem + kRingElems)), par(0),
+          err(err_) {
         gld = (int32_t)g.gld;
         gldr = (int32_t)g.gldr;
         gn = g.gn;
@@ -352,6 +389,9 @@ struct PanelIO {
         gout[POOL_SOUT - POOL_LOUT] = A.Sout + g.gband + lane;
         gout[POOL_QBAR - POOL_LOUT] = A.Qbar + g.gband + lane;
         gout[POOL_XOUT - POOL_LOUT] = A.Xout + g.grhs + r0 + lane;
+        bulk_ok = true;
+#pragma unroll
+        for (int S = 0; S < NIN; ++S) bulk_ok = bulk_ok && active(SW::in_spec(S));
     }
 
     __device__ static __forceinline__ int wrap_add(int x, int d) {
@@ -392,13 +432,56 @@ struct PanelIO {
         for (int S = 0; S < NIN; ++S) issue<ALL>(S, m, q);
     }
     __device__ __forceinline__ void issue_tile(int64_t m, int q) {
-        if (m * TW + min_off() >= 0 && m * TW + TW + max_off() <= gn) issue_all<true>(m, q);
+        const bool inside = m * TW + min_off() >= 0 && m * TW + TW + max_off() <= gn;
+        if constexpr (BULK) {
+            if (inside && bulk_ok) {
+                // one thread arms the slot's barrier and copies every stream's block whole
+                if (lane == 0) {
+                    fence_proxy_async_smem();        // the lanes' earlier reads of the slot come first
+                    mbar_arrive_expect_tx(bars + q, (uint32_t)(NIN * kTileElems * sizeof(T)));
+#pragma unroll
+                    for (int S = 0; S < NIN; ++S) {
+                        const StreamSpec s = SW::in_spec(S);
+                        const int64_t c0 = m * TW + s.off;
+                        bulk_g2s(ring + (S * R + q) * kTileElems, gin[s.pool] + row_off(s) + (int32_t)c0 * kWarp,
+                                 (uint32_t)(kTileElems * sizeof(T)), bars + q);
+                    }
+                }
+                return;
+            }
+            // edge tiles (zero fill) and partially active launches: the pieces, and a plain
+            // arrival so that the slot's barrier phase completes
+            if (inside) issue_all<true>(m, q);
+            else issue_all<false>(m, q);
+            if (lane == 0) mbar_arrive(bars + q);
+            return;
+        }
+        if (inside) issue_all<true>(m, q);
         else issue_all<false>(m, q);
+    }
+    // BULK: wait for the next phase of slot q (bounded; a wait that gives up is counted)
+    __device__ __forceinline__ void wait_slot(int q) {
+        const uint32_t ph = (par >> q) & 1u;
+        uint32_t spins = 0;
+        while (!mbar_test_wait(bars + q, ph)) {
+            if (++spins >= kBulkSpinLimit) {
+                if (lane == 0 && err) atomicAdd(err, 1u);
+                break;
+            }
+        }
+        par ^= 1u << q;
     }
 
     __device__ void begin_tiles(int64_t m0, int64_t, int64_t) {
         cR = (int)(((m0 % R) + R) % R);
         iR = cR;
+        if constexpr (BULK) {
+            if (lane == 0) {
+                for (int q = 0; q < R; ++q) mbar_init(bars + q, 1);
+                mbar_init_fence();
+            }
+            __syncwarp();
+        }
         for (int t = 0; t < R - 1; ++t) {
             issue_tile(m0 + DIR * t, iR);
             cp_async_commit();
@@ -412,6 +495,7 @@ struct PanelIO {
         cp_async_commit();
         iR = wrap_add(iR, DIR);
         cp_async_wait<R - 1>();
+        if constexpr (BULK) wait_slot(cR);   // the whole-block copies of tile m have landed
         __syncwarp();                      // the other lanes' pieces of tile m have landed
         cur = ring + cR * kTileElems + lane;
         cR = wrap_add(cR, DIR);
@@ -439,7 +523,19 @@ struct PanelIO {
     }
 
     __device__ __forceinline__ void tile_end(int64_t, bool) {}
-    __device__ void finish() { cp_async_wait<0>(); }
+    __device__ void finish() {
+        cp_async_wait<0>();
+        if constexpr (BULK) {
+            // the R - 1 tiles issued ahead of the last one are still owed to their barriers:
+            // wait for them, so that no copy is left in flight into this block's shared memory
+            int q = cR;
+            for (int t = 0; t < R - 1; ++t) {
+                wait_slot(q);
+                q = wrap_add(q, DIR);
+            }
+            __syncwarp();
+        }
+    }
 };
 
 }  // namespace bnd

@@ -14,10 +14,16 @@ namespace bnd {
 // rows (StagedIO); panel plans stage the group's interleaved columns with the
 // whole warp (PanelIO), so idle lanes stay in the loop.
 // ---------------------------------------------------------------------------
+// Panel tiles by whole-block bulk copies completing on shared-memory barriers
+// instead of per-lane 16-byte cp.async pieces (a build option: measured slower
+// on the uneven batch, see the design notes).
+#ifndef BND_PANEL_BULK
+#define BND_PANEL_BULK 0
+#endif
 template <typename T, int L, int K, int FL, bool FWD, bool PANEL>
 struct StagedIOOf {
     using SW = typename SweepOf<T, L, K, FL, FWD>::type;
-    using type = typename std::conditional<PANEL, PanelIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>,
+    using type = typename std::conditional<PANEL, PanelIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1, BND_PANEL_BULK != 0>,
                                            StagedIO<T, SW, RingDepth<L>::R, FWD ? 1 : -1>>::type;
 };
 
@@ -58,7 +64,7 @@ staged_kernel(PlanDev P, SweepArgs<T> A, int32_t task0, int32_t ntasks, int32_t 
         const ChainCtx c = run ? make_ctx(P, ch.inst, ch.seg) : idle_ctx();
         const T *exact = (run && rerun) ? exact_start<T, FWD>(P, c) : nullptr;
         const ChainPtrs<T> ptrs = chain_ptrs(A, c);
-        IO io(ptrs, A, tk, wsm, lane);
+        IO io(ptrs, A, tk, wsm, lane, P.counters + kTimeoutCounter);
         run_reg<T, L, K, FL, FWD>(P, A, c, mode, exact, io);
     } else {
         if (ch.inst < 0 || !mine) return;
