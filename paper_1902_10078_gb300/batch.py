@@ -215,17 +215,18 @@ def _cuda_timer(fn, reps, warmup):
     return a.elapsed_time(b) / reps
 
 
-# Default candidates: segment length x warm-up slope (rows per unit of bandwidth,
-# plus 32), the direct kernels at the library defaults, and no segmentation at
-# all (for inputs whose cold starts converge too slowly: every segment would be
-# rerun after the parallel pass).
+# Default candidates: the library defaults, segment length x warm-up slope (rows
+# per unit of bandwidth, plus 32), the direct kernels at the library defaults,
+# and no segmentation at all (for inputs whose cold starts converge too slowly:
+# every segment would be rerun after the parallel pass).
 DEFAULT_CANDIDATES = tuple(
-    [dict(seg_len=s, warm_per_l=w, warm_base=32) for s in (256, 384, 512, 768) for w in (12, 16, 24)]
+    [dict()]
+    + [dict(seg_len=s, warm_per_l=w, warm_base=32) for s in (256, 384, 512, 768) for w in (12, 16, 24)]
     + [dict(flags=1), dict(seg_len=-1)])
 
 
 def _candidate_key(c):
-    return ",".join(f"{k}={c[k]}" for k in sorted(c))
+    return ",".join(f"{k}={c[k]}" for k in sorted(c)) or "library defaults"
 
 
 def autotune(layout, make_step, candidates=DEFAULT_CANDIDATES, reps=3, warmup=2, use_cache=True,

@@ -39,20 +39,21 @@ def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
 
 
 def test_autotune_searches_segments_warmups_and_kernels(tmp_path, monkeypatch):
-    """The default candidates cover segment length x warm-up slope, the
-    direct kernels and no segmentation; the fastest dict is returned whole."""
+    """The default candidates cover the library defaults, segment length x
+    warm-up slope, the direct kernels and no segmentation; the fastest dict is
+    returned whole."""
     monkeypatch.setenv("BND_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     lay = BT.Layout([5000, 6000, 300], [3, 3, 7], 4, B.BND_F32, panels=True)
 
     def cost(tuning):
-        if tuning.get("flags") or tuning["seg_len"] < 0:
+        if not tuning or tuning.get("flags") or tuning["seg_len"] < 0:
             return 9.0
         return abs(tuning["seg_len"] - 512) / 100 + abs(tuning["warm_per_l"] - 16)
 
     tuning, timings = BT.autotune(lay, lambda plan: plan.tuning, plan_factory=FakePlan,
                                   timer=lambda t, reps, warmup: cost(t))
     assert tuning == {"seg_len": 512, "warm_per_l": 16, "warm_base": 32}
-    assert len(timings) == len(BT.DEFAULT_CANDIDATES) == 14
+    assert len(timings) == len(BT.DEFAULT_CANDIDATES) == 15
 
 
 def test_signature_separates_workloads():
