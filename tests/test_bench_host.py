@@ -71,3 +71,12 @@ def test_strong_scaling_layouts_cover_the_batch_once():
             assert seeds[p] == W.BASE_SEED + i
         seen += order
     assert sorted(seen) == list(range(count))
+
+
+def test_source_hash_ignores_comments_only():
+    """The stored traffic stays valid across comment edits of the hot sources,
+    not across code edits."""
+    code = "int f(int x) {\n    return x + 1;  // one more\n}\n/* block\n comment */\n"
+    assert bench._code_only(code) == bench._code_only(code.replace("one more", "the successor"))
+    assert bench._code_only(code) == bench._code_only("int f(int x) {\n\n    return x + 1;\n}\n")
+    assert bench._code_only(code) != bench._code_only(code.replace("x + 1", "x + 2"))
