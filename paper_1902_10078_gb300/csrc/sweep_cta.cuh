@@ -697,11 +697,13 @@ __device__ void run_bwd_cta(const PlanDev &P, const SweepArgs<T> &A, const Chain
                     const T *lcol = sLw.col(e, st);               // column m = j - e of L
                     wc = W + wrap_slot(sj - e, lw) * rs;           // its pending L-bar
                     ljm = lcol[e * st];                            // L[j, m]
-                    const int dl = dmax < l - e ? dmax : l - e;              // L[j+d, m] inside the band
-                    for (int d = 1 + g; d <= dl; d += G) {
+                    const int dl = dmax < l - e ? dmax : l - e;    // L[j+d, m] inside the band
+                    const T *pl = lcol + (int64_t)(1 + g + e) * st; // L[j+d, m], d = 1 + g, 1 + g + G, ...
+                    const int64_t pstep = (int64_t)G * st;
+                    for (int d = 1 + g; d <= dl; d += G, pl += pstep) {
                         const T qb = rw[d];
                         wc[d + e] = fma(-qb, ljm, wc[d + e]);
-                        acc = fma(qb, lcol[(d + e) * st], acc);
+                        acc = fma(qb, *pl, acc);
                     }
                 }
                 for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
