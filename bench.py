@@ -632,9 +632,12 @@ def run_config(args):
     peaks = compute_peaks()
     if args.config == 0:
         import oracle as O
+        tuning = {key: v for key, v in (("seg_len", args.seg_len), ("warm_per_l", args.warm_per_l),
+                                         ("warm_base", args.warm_base)) if v}
         for name, dt in dts.items():
-            lay, plan, step, info = gmm_setup([(1000, 2)], 1, dt)
+            lay, plan, step, info = gmm_setup([(1000, 2)], 1, dt, tuning or None)
             ms = timed(step, 200)
+            fix = sum(B.bnd_plan_fixups(plan.handle, kk) for kk in range(6))
             ins = W.make_instance(1000, 2, 1, W.BASE_SEED)
             O.lib()
             reps, t0 = 200, time.perf_counter()
@@ -643,7 +646,8 @@ def run_config(args):
             cpu_us = 1e6 * (time.perf_counter() - t0) / reps
             lines.append({"config": f"plain single instance n=1000, l=2, 1 RHS, {name}: fused Cholesky + solve + "
                           "log-det + subset inverse, forward and backward", "us_per_step": 1e3 * ms,
-                          "segments": plan.chains, "oracle_us_per_step_1core": cpu_us,
+                          "segments": plan.chains, "segment_fixups_last_step": fix, "tuning": tuning,
+                          "oracle_us_per_step_1core": cpu_us,
                           "bound": "the per-row dependent chain of each segment (FP64: ~650-cycle sqrt and "
                                    "division, 64-cycle FMA on this part)"})
     elif args.config == 1:
