@@ -251,7 +251,9 @@ def fill_pools(lay, seeds, workers=1):
 # reordering).  Synthetic stand-in: a random geometric graph in a rectangle of
 # unit area (aspect ratio `aspect`), precision kappa^2 I + graph Laplacian
 # (SPD), nodes reordered by reverse Cuthill-McKee so that the precision is
-# banded.  At 11284 nodes, mean degree 6 and aspect 2 the band is l = 140.
+# banded.  At 11284 nodes, mean degree 6 and aspect 2 the band is l = 140 with
+# scipy 1.18 (other scipy versions break the ordering's ties differently: 162
+# was seen).
 # ---------------------------------------------------------------------------
 
 def gmrf_graph(N: int, mean_degree: float = 6.0, kappa2: float = 0.1, aspect: float = 2.0,
